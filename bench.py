@@ -1,0 +1,410 @@
+"""Benchmark: FP64 ABAC-preconditioned MINRES solves of the 2D wave workload.
+
+Workload (one "step" = one full solve of the hot path): 2D wave u_tt = Lap u + f on
+[0,1]^2, 5-point Laplacian on a 255 x 255 interior grid, 256 time levels, T = 1,
+manufactured u = sin(pi x) sin(pi y) cos(sqrt(2) pi t) with seeded U[-1,1]*1e-3 source
+noise (16,646,400 unknowns), alpha = 1e-6, MINRES from a zero guess to a TRUE
+relative residual of 1e-8; each step builds b = Y f from the resident inputs
+(f, psi0, psi1 already in HBM) and solves.  FP64 end to end.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas (one problem
+per GPU, no data-path collective; weak scaling) under torch.distributed.run.
+--impl reference times the CPU oracle (the paper's method written plainly in
+NumPy) on the same workload: each step is a bounded sample, one MINRES
+iteration's operator work (one P_alpha^{-1} application and two Y T
+applications), scaled to solves/s by the oracle's own iteration count.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("MINRES solves/s & unknown·iters/s at rel-res 1e-8; "
+          "precond-apply HBM GB/s vs 8 TB/s")
+WORKLOAD = dict(d=2, N=255, nt=256, alpha=1e-6, rtol=1e-8, maxit=100, seed=2)
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def log2(v):
+    return v.bit_length() - 1
+
+
+def algorithmic_flops(cls: str, d: int, N: int, nt: int, unknowns: int) -> float:
+    """Algorithmic FLOPs of one launch of a kernel class (standard FFT count
+    5 L log2 L per complex transform of length L, i.e. 2.5 L log2 L per real one)."""
+    M = N + 1
+    if cls.startswith("time"):
+        # 4 real transforms of length n, two spectral multiplies (6 flops per complex
+        # value = 6 per real unknown), three diagonal scalings
+        return unknowns * (4 * 2.5 * log2(nt) + 6 + 3)
+    if cls.startswith("dst"):
+        # DST-I of length N counted as one real transform of length N+1
+        return unknowns * 2.5 * log2(M)
+    if cls in ("yt", "yt_dot", "yt_res"):
+        return unknowns * (2 * d + 3 + (1 if cls != "yt" else 0))
+    return 0.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0, period_ms: int = 100):
+        self.proc = None
+        self.path = None
+        self.index = index
+        self.period = period_ms
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", f"-lms", str(self.period)],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(cls: str):
+    """ncu DRAM bytes per launch for the dominant kernel, if captured for the
+    current kernel source (profiles/traffic.json, written from an ncu capture)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    r = rec.get(cls)
+    if not r:
+        return None
+    srcs = [os.path.join(ROOT, "paper_2306_03574_gb300", "csrc", f) for f in r.get("sources", [])]
+    try:
+        if source_hash(srcs) != r.get("source_hash"):
+            return None
+    except Exception:
+        return None
+    return r.get("bytes_per_launch")
+
+
+def dist_setup(n_gpus: int, backend: str):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_problem():
+    import workloads as W
+    from oracle import fast as OF
+    from oracle import system as OS
+    p = W.config_2d(N=WORKLOAD["N"], nt=WORKLOAD["nt"], alpha=WORKLOAD["alpha"], seed=WORKLOAD["seed"])
+    pc = OF.ABACPreconditioner(2, p.N, p.nt, p.tau, p.alpha)
+    A = lambda v: OS.apply_YT(v, 2, p.N, p.tau)
+    return p, pc, A
+
+
+def oracle_full_solve(p, pc, A):
+    """One full oracle solve (rhs + MINRES to true rel-res 1e-8); returns (seconds, iters)."""
+    from oracle import minres as OM
+    from oracle import system as OS
+    t0 = time.perf_counter()
+    b = OS.rhs_b(p)
+    x, info = OM.minres(A, pc.apply, b, rtol=WORKLOAD["rtol"], maxit=WORKLOAD["maxit"])
+    return time.perf_counter() - t0, info["iters"]
+
+
+def oracle_iteration_sample(p, pc, A, v):
+    """One MINRES iteration's operator work of the oracle: P^{-1} v, Y T z, Y T x."""
+    t0 = time.perf_counter()
+    z = pc.apply(v)
+    A(z)
+    A(v)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+    p, pc, A = oracle_problem()
+    from oracle import system as OS
+    v = OS.rhs_b(p)
+    # warm-up: the first one is a full oracle solve, which also gives the iteration count
+    t_full, iters = oracle_full_solve(p, pc, A)
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_iteration_sample(p, pc, A, v)
+    ts = [oracle_iteration_sample(p, pc, A, v) for _ in range(args.steps)]
+    t_step = float(np.mean(ts))
+    # a solve = rhs + one P^{-1} at start + iters x (P^{-1} + 2 Y T): ~ (iters + 1) samples
+    t_solve = t_step * (iters + 1)
+    value = 1.0 / t_solve
+    cores = os.cpu_count()
+    unknowns = p.nt * p.m
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(unknowns),
+        "iters_per_solve": iters, "unknown_iters_per_s": unknowns * iters / t_solve,
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"per step one oracle MINRES iteration's operator work at full size "
+                                   f"(1 P^-1 + 2 YT), scaled by (iters+1)={iters + 1}; one full oracle "
+                                   f"solve in warm-up took {t_full:.2f} s"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(unknowns):
+    return {"workload": "2d_wave_N255_nt256_fp64_minres_relres1e-8", "d": 2, "N": WORKLOAD["N"],
+            "nt": WORKLOAD["nt"], "unknowns": unknowns, "alpha": WORKLOAD["alpha"],
+            "rtol": WORKLOAD["rtol"], "rhs": 1, "seed": WORKLOAD["seed"],
+            "l2": "inputs larger than L2: every vector is 133 MB (L2 126 MB), ~1.2 GB touched per step",
+            "parallelism": "replicas (one independent problem per GPU)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2306_03574_gb300 as aao
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p = W.config_2d(N=WORKLOAD["N"], nt=WORKLOAD["nt"], alpha=WORKLOAD["alpha"],
+                    seed=WORKLOAD["seed"] + 1000 * rank)
+    unknowns = p.nt * p.m
+    f = torch.from_numpy(p.f).to(dev)
+    psi0 = torch.from_numpy(p.psi0).to(dev)
+    psi1 = torch.from_numpy(p.psi1).to(dev)
+    b = torch.empty((p.nt, p.m), dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    s = aao.Solver(2, p.N, p.nt, p.tau, p.alpha)
+    rtol, maxit = WORKLOAD["rtol"], WORKLOAD["maxit"]
+
+    def step():
+        s.build_rhs(f, psi0, psi1, b, stream=stream)
+        st, info = s.solve(b, x, rtol=rtol, maxit=maxit, stream=stream)
+        if st != aao.AAO_OK:
+            raise RuntimeError(f"solve failed: {aao.aao_status_str(st)} {info}")
+        return info[0]
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    aao.aao_profile_enable(s.h, True)
+    l0 = s.launches
+    iters = []
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        iters.append(step()["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    launches = s.launches - l0
+    prof = aao.aao_profile_read(s.h)
+    aao.aao_profile_enable(s.h, False)
+    clk = clocks.stop()
+    ms_max = reduce_max(ms, world, dev)
+    value = world * args.steps / (ms_max / 1e3)
+    it = float(np.mean(iters))
+    relres = info["relres_true"]
+
+    # ---- per-kernel roofline (live CUDA-event timing in the timed region) ----
+    kern = {k: {"launches": v[0], "total_ms": round(v[1], 4), "avg_ms": v[1] / max(v[0], 1),
+                "share": v[1] / max(sum(t for _, t in prof.values()), 1e-12)} for k, v in prof.items()}
+    dom = max(kern, key=lambda k: kern[k]["total_ms"])
+    flops = algorithmic_flops(dom, 2, p.N, p.nt, unknowns)
+    achieved = flops / (kern[dom]["avg_ms"] / 1e3) / 1e12
+    peak = FP64_PEAK_TFLOPS if dom.endswith("f64") or dom.startswith("yt") else FP32_PEAK_TFLOPS
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_record(dom),
+                "flops_per_launch": flops,
+                "peak_note": "FP64 CUDA-core peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
+    for k in kern:
+        fl = algorithmic_flops(k, 2, p.N, p.nt, unknowns)
+        if fl:
+            kern[k]["achieved_tflops"] = fl / (kern[k]["avg_ms"] / 1e3) / 1e12
+    # preconditioner application as a whole, against HBM (16 B per unknown in + out)
+    prec_cls = [k for k in kern if k.startswith("dst") or k.startswith("time")]
+    applies = kern.get("time_f64", {}).get("launches", 0)
+    prec_ms = sum(kern[k]["total_ms"] for k in prec_cls) / max(applies, 1)
+    hbm = measured_peaks().get("hbm_gbs", 6777.0)
+    prec = {"ms_per_apply": prec_ms, "algorithmic_bytes": 16 * unknowns,
+            "hbm_gbs": 16 * unknowns / (prec_ms / 1e3) / 1e9 if prec_ms else None}
+    prec["frac_of_measured_hbm"] = prec["hbm_gbs"] / hbm if prec["hbm_gbs"] else None
+    prec["frac_of_8tbs"] = prec["hbm_gbs"] / 8000.0 if prec["hbm_gbs"] else None
+
+    # ---- end to end through the C ABI with host buffers ----
+    fh = torch.from_numpy(p.f.copy()).pin_memory()
+    p0h = torch.from_numpy(p.psi0.copy()).pin_memory()
+    p1h = torch.from_numpy(p.psi1.copy()).pin_memory()
+    uh = torch.empty((p.nt, p.m), dtype=torch.float64).pin_memory()
+    s.solve_host(fh, p0h, p1h, uh, rtol=rtol, maxit=maxit, stream=stream)  # staging warm-up
+    e2e_steps = max(1, min(args.steps, 20))
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st, inf2 = s.solve_host(fh, p0h, p1h, uh, rtol=rtol, maxit=maxit, stream=stream)
+        if st != aao.AAO_OK:
+            raise RuntimeError(f"host solve failed {inf2}")
+    torch.cuda.synchronize(dev)
+    t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
+    barrier(world)
+    e2e = {"value": world * e2e_steps / t_e2e, "unit": "solves/s",
+           "h2d_bytes_per_step": 8 * (p.nt * p.m + 2 * p.m), "d2h_bytes_per_step": 8 * p.nt * p.m,
+           "steps": e2e_steps, "api": "aao_solve_host"}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            pp, pc, A = oracle_problem()
+            t_full, it_o = oracle_full_solve(pp, pc, A)
+            cpu = {"value": 1.0 / t_full, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"one full oracle solve of the same workload (rhs + MINRES, {it_o} iterations, "
+                             f"NumPy/BLAS on all host cores), {t_full:.2f} s; preconditioner setup excluded"}
+        out = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(unknowns),
+            "iters_per_solve": it, "relres_true": relres,
+            "unknown_iters_per_s": world * unknowns * it * args.steps / (ms_max / 1e3),
+            "prec_apply": prec, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk, "kernels": kern,
+        }
+        print(json.dumps(out), flush=True)
+    s.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    if args.impl == "reference":
+        world, rank, local = dist_setup(args.gpus, "gloo")
+        rc = run_reference(args, world, rank)
+    else:
+        world, rank, local = dist_setup(args.gpus, "nccl")
+        rc = run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

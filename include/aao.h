@@ -1,0 +1,207 @@
+/*
+ * aao.h -- C ABI of the GB300 all-at-once wave solver (libaao.so).
+ *
+ * The library solves the symmetrised all-at-once system of the implicit
+ * leap-frog discretisation of the wave equation
+ *
+ *     u_tt = c^2 Lap u + f   on (0,1)^d x (0,T],  u = 0 on the boundary,
+ *     u(0) = psi0, u_t(0) = psi1                      (paper, eq. (1.1))
+ *
+ * by preconditioned MINRES on  Y T u = Y f  (eqs. (main_matrix), (symmetricform))
+ * with the absolute-value block alpha-circulant preconditioner
+ * P_alpha = (C_alpha^{1/2})^T C_alpha^{1/2}  (def. (matrix_P), eq. (precsys)).
+ *
+ * Conventions shared by every entry point
+ *   - grid: d in {1,2,3}; N interior points per axis, the same on every axis;
+ *     h = 1/(N+1); m = N^d spatial unknowns in lexicographic order, x fastest.
+ *   - time: nt = n time levels u^(1..n), tau = T/n (the caller passes tau).
+ *   - vectors: FP64, time-major, index (rhs, i, s) -> (rhs*n + i)*m + s with
+ *     i = 0..n-1 standing for u^(i+1).  A batch of nrhs vectors is contiguous.
+ *   - pointers are DEVICE pointers unless an entry point says otherwise; they
+ *     are owned by the caller and must stay valid until the stream reaches the
+ *     end of the call.  Alignment: 8 bytes.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are stream-ordered and asynchronous except where stated.
+ *   - errors: every call returns an aao_status; nothing is thrown across the
+ *     ABI.  aao_last_error() gives a thread-local text for the last failure.
+ *   - a handle may be used from one host thread at a time.
+ */
+#ifndef AAO_H_
+#define AAO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum aao_status {
+  AAO_OK = 0,
+  AAO_EINVAL = 1,        /* bad argument (null pointer, alpha outside (0,1], tau <= 0, ...) */
+  AAO_EUNSUPPORTED = 2,  /* size outside what the kernels implement (see aao_create) */
+  AAO_ENOMEM = 3,        /* device allocation failed, or a request exceeds a budget */
+  AAO_ECUDA = 4,         /* a CUDA runtime call failed; aao_last_error() has the text */
+  AAO_ENOTCONV = 5,      /* MINRES reached maxit before the residual tolerance */
+  AAO_EBREAKDOWN = 6,    /* MINRES breakdown: <z, v> < 0 (preconditioner not SPD in floating point) */
+  AAO_ESINGULAR = 7,     /* preconditioner singular: min |Sigma| below the threshold (alpha = 1 only) */
+  AAO_EBUSY = 8,         /* serving: no free slot */
+  AAO_EPENDING = 9,      /* serving: request not finished yet */
+  AAO_ETIMEOUT = 10      /* a bounded wait ran out */
+} aao_status;
+
+/* Spatial grid: Omega = (0,1)^dim, N interior points per axis (equal spacing on
+ * every axis, as in the paper's Section 3), wave speed squared c2 (1 in the paper;
+ * L = I - (c2 tau^2 / 2) Delta_h, i.e. the mean-coefficient form of eq.
+ * (mean-coefftsmat) with a-bar = c2). */
+typedef struct aao_grid {
+  int dim;
+  int N;
+  double c2;
+} aao_grid;
+
+/* Time discretisation: the implicit leap-frog scheme of Section 1 (the only one). */
+typedef enum aao_scheme { AAO_SCHEME_IMPLICIT_LEAPFROG = 0 } aao_scheme;
+
+/* Precision of the preconditioner application. */
+typedef enum aao_precision {
+  AAO_PREC_FP64 = 0,     /* everything in FP64 */
+  AAO_PREC_FP32_IR = 1   /* P_alpha^{-1} in FP32/complex64; operator, MINRES recurrences,
+                            residuals and an outer iterative refinement in FP64 */
+} aao_precision;
+
+typedef struct aao_opts {
+  int precision;         /* aao_precision, default AAO_PREC_FP64 */
+  int nrhs_max;          /* largest batch passed to any call; workspace is sized for it (default 1) */
+  int reserved[6];       /* must be zero */
+} aao_opts;
+
+typedef struct aao_solve_info {
+  int iters;             /* MINRES iterations (summed over refinement steps in FP32_IR mode) */
+  int status;            /* aao_status of this right-hand side */
+  double relres_true;    /* ||b - Y T x||_2 / ||b||_2, recomputed explicitly */
+  double relres_est;     /* MINRES recurrence estimate ||r||_{P^-1} / ||r_0||_{P^-1} */
+  int ir_steps;          /* outer refinement steps (FP32_IR mode), else 0 */
+  int reserved;
+} aao_solve_info;
+
+typedef struct aao_handle aao_handle;
+
+/* Create a solver for one (grid, nt, tau, alpha) and allocate all its device
+ * memory (tables + workspace); this is the only allocating call besides the
+ * serving API.  Builds, on the device, the spectral factors
+ * Sigma_{k,j}^{-1/2} = (Lambda_j lambda_{1,k} + lambda_{2,k})^{-1/2} with the
+ * principal branch (eqs. (calphaprediagform), (calphasqrtdiagform); Section 2.3).
+ *   grid  : host pointer; dim in {1,2,3}; N+1 a power of two, 64 <= N+1 <= 512
+ *           (so N in {63,127,255,511}); c2 > 0.
+ *   nt    : number of time levels n; a power of two, 64 <= nt <= 1024.
+ *   tau   : time step (> 0), normally T/nt.
+ *   alpha : in (0, 1]; alpha = 1 gives the ABC preconditioner |C_1| (Remark
+ *           p1badpermformremark) and returns AAO_ESINGULAR if some |Sigma| is
+ *           below 1e-12 * max|Sigma| (Remark c1badperformremark).
+ *   scheme: AAO_SCHEME_IMPLICIT_LEAPFROG.
+ *   opts  : host pointer or NULL for defaults.
+ *   out   : receives the handle (host pointer).
+ * Synchronous on the current device.  Errors: AAO_EINVAL, AAO_EUNSUPPORTED,
+ * AAO_ENOMEM, AAO_ECUDA, AAO_ESINGULAR. */
+aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha,
+                      aao_scheme scheme, const aao_opts* opts, aao_handle** out);
+
+/* Free the handle and all its device memory (synchronises its device). */
+aao_status aao_destroy(aao_handle* h);
+
+/* Bytes of device memory held by the handle (tables + workspace). */
+size_t aao_workspace_bytes(const aao_handle* h);
+
+/* Build b = Y f from the data of eq. (main_matrix):
+ *   f    : nrhs x n x m, f[k] = f(G_h, k tau), k = 0..n-1 (source samples);
+ *   psi0 : nrhs x m, psi1: nrhs x m (initial value and velocity);
+ *   b    : nrhs x n x m output, the time-reversed right-hand side
+ *          tau^2 [f^0/2 + psi1/tau + psi0/tau^2; f^1 - L psi0/tau^2; f^2; ...; f^(n-1)].
+ * Device pointers; b must not alias the inputs.  Errors: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_build_rhs(aao_handle* h, const double* f, const double* psi0,
+                         const double* psi1, double* b, int nrhs, void* stream);
+
+/* y = Y T x (eq. (main_system)): (T x)_i = L x_i - 2 x_{i-1} + L x_{i-2} with
+ * x_{-1} = x_{-2} = 0, L = I - (c2 tau^2/2) Delta_h the (2d+1)-point Dirichlet
+ * stencil, and Y reversing the time levels (Section 2.3, first paragraph).
+ * x, y: nrhs x n x m device vectors, must not alias.  Errors: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_apply_op(aao_handle* h, const double* x, double* y, int nrhs, void* stream);
+
+/* z = P_alpha^{-1} r = C_alpha^{-1/2} (C_alpha^{-1/2})^T r by Section 2.3's
+ * three-step procedure done twice: a DST along each spatial axis, per spatial
+ * mode the time pipeline D^{-1} -> FFT -> x Sigma^{-1/2} -> iFFT -> D^2 ->
+ * FFT -> x conj(Sigma^{-1/2}) -> iFFT -> D^{-1}, then the DSTs again.
+ * r, z: nrhs x n x m device vectors; z may equal r (in place).  Uses the
+ * handle's precision.  Errors: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_apply_prec(aao_handle* h, const double* r, double* z, int nrhs, void* stream);
+
+/* y = (I_n (x) U) x with U = S (x) ... (x) S the orthonormal multi-dimensional
+ * DST-I (Section 2.3: on a uniform grid the eigenvector matrix U of L is the
+ * DST); U = U^T = U^{-1}.  This is the spatial part of P_alpha^{-1}, exposed on
+ * its own.  x, y: nrhs x n x m, may be equal.  FP64.  Errors: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_apply_dst(aao_handle* h, const double* x, double* y, int nrhs, void* stream);
+
+/* The time part of P_alpha^{-1} on DST coefficients: for every spatial mode j
+ * the n x n map D^{-1} F^* G_j F D^2 F G_j F^* D^{-1} (G_j = diag of
+ * Sigma_{k,j}^{-1/2}; Section 2.3 with U factored out), so that
+ * apply_prec = apply_dst o apply_time o apply_dst.  x, y may be equal.  FP64.
+ * Errors: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_apply_time(aao_handle* h, const double* x, double* y, int nrhs, void* stream);
+
+/* Preconditioned MINRES on Y T x = b with P_alpha (eq. (precsys); Section 3:
+ * MINRES, relative-residual stopping).  Stops for each right-hand side at the
+ * first iteration whose TRUE relative residual ||b - Y T x||_2/||b||_2 <= rtol
+ * (recomputed every iteration), or at maxit.
+ *   b      : nrhs x n x m device input (unchanged).
+ *   x      : nrhs x n x m device in/out: the initial guess if use_x0 != 0
+ *            (else ignored and zero is used, as in the paper), the solution on return.
+ *   info   : host array of nrhs records (may be NULL).
+ * Blocks the calling thread until the solve finishes (it reads a small status
+ * block every iteration).  Returns AAO_OK if every right-hand side converged,
+ * else the first failing status (AAO_ENOTCONV, AAO_EBREAKDOWN), with info
+ * filled in either case.  Errors also: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_minres_solve(aao_handle* h, const double* b, double* x, int use_x0, int nrhs,
+                            double rtol, int maxit, aao_solve_info* info, void* stream);
+
+/* End-to-end solve from HOST buffers: copies f, psi0, psi1 (host, any memory;
+ * pinned for speed) to the device, builds b (aao_build_rhs), runs
+ * aao_minres_solve from a zero guess, and copies u (host, nrhs x n x m) back.
+ * Blocks until u is on the host.  Errors as aao_minres_solve. */
+aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, const double* psi1,
+                          double* u, int nrhs, double rtol, int maxit,
+                          aao_solve_info* info, void* stream);
+
+/* Number of kernel launches this handle has issued since creation (statistics). */
+uint64_t aao_launch_count(const aao_handle* h);
+
+/* Per-kernel timing (statistics, not part of the method).  While enabled, every
+ * kernel the handle launches is bracketed by two CUDA events recorded on the
+ * stream it is launched on; aao_profile_read synchronises on those events and
+ * returns, per kernel class, the launch count and the summed event time. */
+typedef struct aao_kernel_stat {
+  char name[32];         /* kernel class, e.g. "dst_x_f64", "time_f64", "yt_dot" */
+  uint64_t launches;
+  double total_ms;
+} aao_kernel_stat;
+
+/* on != 0: clear the records and start recording; on == 0: stop recording
+ * (records are kept until the next enable).  Errors: AAO_EINVAL. */
+aao_status aao_profile_enable(aao_handle* h, int on);
+
+/* Fill out[0..max) with the classes seen since the last enable (host array) and
+ * return how many there are (may exceed max), or -1 on error.  Blocks until
+ * every recorded event has completed. */
+int aao_profile_read(aao_handle* h, aao_kernel_stat* out, int max);
+
+/* Text of a status code (static storage). */
+const char* aao_status_str(aao_status s);
+
+/* Thread-local text of the last failure in this thread ("" if none). */
+const char* aao_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AAO_H_ */

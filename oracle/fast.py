@@ -19,6 +19,12 @@ Readings of the paper adopted here (each pinned by a test):
     of the I-term is already inside lambda_{2,k} (as in eq. (calphaprediagform)
     and Appendix A); Step 2's extra "(-2 I_m)" is not applied a second time.
   * Sigma^{-1/2} uses the principal branch (eq. (calphasqrtdiagform)).
+  * Sigma_{k,j} = Lambda_j lambda_{1,k} + lambda_{2,k} is evaluated in the algebraically
+    identical form (1 - a theta^k)^2 + (Lambda_j - 1)(1 + a^2 theta^{2k}), a = alpha^{1/n},
+    with 1 - a = -expm1(log(alpha)/n), 1 - cos(phi) = 2 sin^2(phi/2) and Lambda_j - 1 =
+    (c^2 tau^2/2) mu_j taken directly.  The literal form loses up to ~1e-11 relative
+    accuracy by cancellation when Lambda_j ~ 1 and a ~ 1 (low spatial modes, large n);
+    the rewritten form is pinned against the literal formula in 50-digit arithmetic.
   * U = S (x) ... (x) S with S the orthonormal DST-I matrix (Section 2.3: on a
     uniform grid U is the multi-dimensional discrete sine transform).
 No FFT is used: every transform is an explicit matrix product.
@@ -43,22 +49,40 @@ def laplacian_eigenvalues_1d(N: int) -> np.ndarray:
     return 4.0 / (h * h) * np.sin(k * np.pi * h / 2.0) ** 2
 
 
-def L_eigenvalues(d: int, N: int, tau: float, c2: float = 1.0) -> np.ndarray:
-    """Lambda: eigenvalues of L = I - (c^2 tau^2/2) Delta_h in the lexicographic
-    order of the columns of U = S (x) ... (x) S, shape (m,)."""
+def L_eigenvalues_minus_one(d: int, N: int, tau: float, c2: float = 1.0) -> np.ndarray:
+    """Lambda - 1 = (c^2 tau^2/2) * (eigenvalues of -Delta_h), lexicographic order of
+    the columns of U = S (x) ... (x) S, shape (m,)."""
     mu = laplacian_eigenvalues_1d(N)
     tot = np.zeros((N,) * d)
     for a in range(d):
         shp = [1] * d
         shp[d - 1 - a] = N
         tot = tot + mu.reshape(shp)
-    return (1.0 + 0.5 * c2 * tau * tau * tot).ravel()
+    return (0.5 * c2 * tau * tau * tot).ravel()
+
+
+def L_eigenvalues(d: int, N: int, tau: float, c2: float = 1.0) -> np.ndarray:
+    """Lambda: eigenvalues of L = I - (c^2 tau^2/2) Delta_h in the lexicographic
+    order of the columns of U = S (x) ... (x) S, shape (m,)."""
+    return 1.0 + L_eigenvalues_minus_one(d, N, tau, c2)
+
+
+def theta_pow(e, n: int) -> np.ndarray:
+    """theta_n^e = exp(2 pi i e / n) for integer arrays e: the exponent is reduced
+    mod n exactly and the angle functions are evaluated in extended precision
+    (numpy longdouble), then rounded to complex128."""
+    e = np.mod(np.asarray(e, dtype=np.int64), n)
+    ld = np.longdouble
+    ang = ld(2) * ld(np.pi) * e.astype(ld) / ld(n)
+    # long-double pi: refine numpy's double pi by one correction term
+    ang = ang + ld(2) * (ld("3.14159265358979323846264338327950288") - ld(np.pi)) * e.astype(ld) / ld(n)
+    return (np.cos(ang).astype(np.float64) + 1j * np.sin(ang).astype(np.float64))
 
 
 def fourier_matrix(n: int) -> np.ndarray:
     """Unitary F = (1/sqrt(n)) [theta_n^{(i-1)(j-1)}], theta_n = exp(2 pi i / n)."""
     i = np.arange(n)
-    return np.exp(2j * np.pi * np.outer(i, i) / n) / np.sqrt(n)
+    return theta_pow(np.outer(i, i), n) / np.sqrt(n)
 
 
 def D_alpha_diag(n: int, alpha: float) -> np.ndarray:
@@ -69,16 +93,36 @@ def D_alpha_diag(n: int, alpha: float) -> np.ndarray:
 def Lambda_alpha(n: int, alpha: float):
     """lambda_{1,k} = 1 + alpha^{2/n} theta^{2(k-1)}, lambda_{2,k} = -2 alpha^{1/n} theta^{k-1}."""
     k = np.arange(n)
-    theta_k = np.exp(2j * np.pi * k / n)
-    lam1 = 1.0 + alpha ** (2.0 / n) * theta_k ** 2
+    theta_k = theta_pow(k, n)
+    lam1 = 1.0 + alpha ** (2.0 / n) * theta_pow(2 * k, n)
     lam2 = -2.0 * alpha ** (1.0 / n) * theta_k
     return lam1, lam2
 
 
-def Sigma(n: int, alpha: float, Lam: np.ndarray) -> np.ndarray:
-    """Diagonal of Lambda_{alpha,1} (x) Lambda + Lambda_{alpha,2} (x) I_m as an (n, m) array."""
+def Sigma_literal(n: int, alpha: float, Lam: np.ndarray) -> np.ndarray:
+    """Diagonal of Lambda_{alpha,1} (x) Lambda + Lambda_{alpha,2} (x) I_m as an (n, m)
+    array, written exactly as the product and sum of the definitions."""
     lam1, lam2 = Lambda_alpha(n, alpha)
     return lam1[:, None] * Lam[None, :] + lam2[:, None]
+
+
+def Sigma(n: int, alpha: float, Lam_minus_one: np.ndarray) -> np.ndarray:
+    """The same diagonal evaluated without cancellation:
+    Sigma_{k,j} = (1 - a theta^k)^2 + (Lambda_j - 1)(1 + a^2 theta^{2k}), a = alpha^{1/n}
+    (expand the square: 1 - 2 a theta + a^2 theta^2 + (Lambda - 1)(1 + a^2 theta^2)
+    = Lambda (1 + a^2 theta^2) - 2 a theta)."""
+    la = np.log(alpha) / n
+    one_minus_a = -np.expm1(la)
+    a = np.exp(la)
+    k = np.arange(n)
+    th = theta_pow(k, n)                              # theta^k
+    s_half = theta_pow(k, 2 * n).imag                 # sin(phi/2), phi = 2 pi k/n
+    wr = one_minus_a + 2.0 * a * s_half * s_half      # Re(1 - a theta^k) = (1-a) + a (1 - cos phi)
+    wi = -a * th.imag                                 # Im(1 - a theta^k)
+    w2 = (wr - wi) * (wr + wi) + 2j * wr * wi         # (1 - a theta^k)^2
+    qr = one_minus_a * (1.0 + a) + 2.0 * a * a * th.real ** 2   # 1 + a^2 cos(2 phi)
+    q = qr + 1j * a * a * theta_pow(2 * k, n).imag    # 1 + a^2 theta^{2k}
+    return w2[:, None] + Lam_minus_one[None, :] * q[:, None]
 
 
 def apply_space(X: np.ndarray, S: np.ndarray, d: int, N: int) -> np.ndarray:
@@ -98,7 +142,8 @@ class ABACPreconditioner:
     def __init__(self, d: int, N: int, n: int, tau: float, alpha: float, c2: float = 1.0):
         self.d, self.N, self.n, self.alpha = d, N, n, alpha
         self.S = dst_matrix(N)                      # U = S (x) .. (x) S, U = U^T = U^{-1}
-        self.Lam = L_eigenvalues(d, N, tau, c2)
+        self.Lam_m1 = L_eigenvalues_minus_one(d, N, tau, c2)
+        self.Lam = 1.0 + self.Lam_m1
         F = fourier_matrix(n)
         dg = D_alpha_diag(n, alpha)
         FD = F * dg[None, :]                        # F D_alpha
@@ -108,7 +153,7 @@ class ABACPreconditioner:
         self.time_step3_T = FD.T                    # time part of (D^{-1} F^* (x) U)^{-T}
         self.time_right = FD                        # right factor of C^{-1/2}
         self.time_left = DinvFs                     # left factor of C^{-1/2}
-        Sig = Sigma(n, alpha, self.Lam)
+        Sig = Sigma(n, alpha, self.Lam_m1)
         self.Sigma = Sig
         self.g = 1.0 / np.sqrt(Sig)                 # principal branch: Sigma^{-1/2}
 

@@ -1,0 +1,664 @@
+// C ABI of libaao.so: handle management, tables, the P_alpha^{-1} pipeline and
+// the MINRES driver (see include/aao.h for the contract of every entry point).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aao_internal.cuh"
+
+using namespace aao;
+
+namespace {
+
+thread_local std::string g_err;
+
+aao_status fail(aao_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define AAO_CK(expr)                                                                 \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(AAO_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+enum KClass {
+  KC_DST_X64, KC_DST_Y64, KC_DST_Z64, KC_TIME64, KC_DST_X32, KC_DST_Y32, KC_DST_Z32, KC_TIME32,
+  KC_YT, KC_YT_DOT, KC_YT_RES, KC_DOT, KC_VUPD, KC_WXUPD, KC_SCAL, KC_RHS, KC_SUB, KC_CAST,
+  KC_AXPY, KC_TABLE, KC_N
+};
+const char* kc_name(int c) {
+  static const char* names[KC_N] = {
+      "dst_x_f64", "dst_y_f64", "dst_z_f64", "time_f64", "dst_x_f32", "dst_y_f32", "dst_z_f32",
+      "time_f32", "yt", "yt_dot", "yt_res", "dot", "vupdate", "wxupdate", "scalars", "rhs", "sub",
+      "cast", "axpy", "spectral_table"};
+  return (c >= 0 && c < KC_N) ? names[c] : "other";
+}
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct aao_handle {
+  Plan P;
+  int precision = AAO_PREC_FP64;
+  int nrhs_max = 1;
+  int device = 0;
+  uint64_t launches = 0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  // tables
+  double2* tw_space64 = nullptr; double* sinw64 = nullptr; double2* tw_time64 = nullptr;
+  double* dinv64 = nullptr; double* d264 = nullptr; double2* ab64 = nullptr;
+  float2* tw_space32 = nullptr; float* sinw32 = nullptr; float2* tw_time32 = nullptr;
+  float* dinv32 = nullptr; float* d232 = nullptr; float2* ab32 = nullptr;
+  // workspace (nrhs_max * n * m doubles each)
+  double* vT = nullptr; double* vv = nullptr; double* vvp = nullptr; double* vz = nullptr;
+  double* vzn = nullptr; double* vw = nullptr; double* vwp = nullptr;
+  double* vr = nullptr; double* vdx = nullptr;  // refinement (FP32_IR)
+  float* f32 = nullptr;                          // FP32 preconditioner buffer
+  double* partial = nullptr; int partial_stride = 0;  // 3 * nrhs_max * partial_stride
+  MinresScalars* sc = nullptr;
+  MinresScalars* sc_host = nullptr;  // pinned
+  // host-solve staging (allocated on first aao_solve_host)
+  double* hs_f = nullptr; double* hs_psi = nullptr; double* hs_b = nullptr; double* hs_x = nullptr;
+  // kernel timing
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  void clear_prof() {
+    for (auto& r : prof) { ev_pool.push_back(r.a); ev_pool.push_back(r.b); }
+    prof.clear();
+  }
+  ~aao_handle() {
+    clear_prof();
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+    if (sc_host) cudaFreeHost(sc_host);
+  }
+  template <typename T>
+  aao_status alloc(T** p, size_t count) {
+    void* q = nullptr;
+    const size_t b = count * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AAO_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " +
+                                  cudaGetErrorString(e));
+    }
+    allocs.push_back(q);
+    bytes += b;
+    *p = static_cast<T*>(q);
+    return AAO_OK;
+  }
+  size_t vlen() const { return (size_t)P.n * P.m; }
+};
+
+namespace {
+
+#define AAO_TRY(expr)                 \
+  do {                                \
+    aao_status st_ = (expr);          \
+    if (st_ != AAO_OK) return st_;    \
+  } while (0)
+
+// start / stop event of one timed launch (no-ops unless profiling is on)
+int prof_begin(aao_handle* h, int cls, cudaStream_t s) {
+  if (!h->prof_on) return -1;
+  ProfRec r{cls, h->take_event(), h->take_event()};
+  if (!r.a || !r.b) return -1;
+  cudaEventRecord(r.a, s);
+  h->prof.push_back(r);
+  return (int)h->prof.size() - 1;
+}
+void prof_end(aao_handle* h, int idx, cudaStream_t s) {
+  if (idx >= 0) cudaEventRecord(h->prof[idx].b, s);
+}
+
+// launch one kernel through its launcher, timed when profiling is on
+#define AAO_KL(h, cls, s, expr)                 \
+  do {                                          \
+    const int pr_ = prof_begin((h), (cls), (s)); \
+    AAO_CK(expr);                               \
+    prof_end((h), pr_, (s));                    \
+  } while (0)
+
+// host tables in long double, rounded to double
+void host_twiddles(int L, int sign, std::vector<double2>& out) {
+  out.resize(L);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int q = 0; q < L; ++q) {
+    const long double ang = 2.0L * pi * (long double)q / (long double)L;
+    out[q] = make_double2((double)cosl(ang), (double)(sign * sinl(ang)));
+  }
+}
+
+template <typename T>
+aao_status upload(const std::vector<T>& h, T* d) {
+  AAO_CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return AAO_OK;
+}
+
+std::vector<float2> to_f2(const std::vector<double2>& v) {
+  std::vector<float2> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+  return o;
+}
+std::vector<float> to_f(const std::vector<double>& v) {
+  std::vector<float> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+  return o;
+}
+
+aao_status check_handle(const aao_handle* h) {
+  if (!h) return fail(AAO_EINVAL, "null handle");
+  return AAO_OK;
+}
+
+aao_status check_call(aao_handle* h, int nrhs) {
+  AAO_TRY(check_handle(h));
+  if (nrhs < 1 || nrhs > h->nrhs_max)
+    return fail(AAO_EINVAL, "nrhs must be in [1, nrhs_max=" + std::to_string(h->nrhs_max) + "]");
+  AAO_CK(cudaSetDevice(h->device));
+  return AAO_OK;
+}
+
+// P^{-1} applied in the handle's precision: in -> out (FP64 vectors, may alias)
+aao_status prec_apply(aao_handle* h, const double* in, double* out, int nrhs, cudaStream_t s) {
+  const Plan& P = h->P;
+  if (h->precision == AAO_PREC_FP64) {
+    AAO_KL(h, KC_DST_X64, s, launch_dst_axis<double>(P, in, out, 0, nrhs, s, &h->launches));
+    for (int ax = 1; ax < P.d; ++ax)
+      AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
+    AAO_KL(h, KC_TIME64, s, launch_time<double>(P, out, out, nrhs, s, &h->launches));
+    for (int ax = P.d - 1; ax >= 0; --ax)
+      AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
+  } else {
+    const size_t cnt = (size_t)nrhs * h->vlen();
+    AAO_KL(h, KC_CAST, s, launch_cast(in, h->f32, cnt, s, &h->launches));
+    for (int ax = 0; ax < P.d; ++ax)
+      AAO_KL(h, KC_DST_X32 + ax, s, launch_dst_axis<float>(P, h->f32, h->f32, ax, nrhs, s, &h->launches));
+    AAO_KL(h, KC_TIME32, s, launch_time<float>(P, h->f32, h->f32, nrhs, s, &h->launches));
+    for (int ax = P.d - 1; ax >= 0; --ax)
+      AAO_KL(h, KC_DST_X32 + ax, s, launch_dst_axis<float>(P, h->f32, h->f32, ax, nrhs, s, &h->launches));
+    AAO_KL(h, KC_CAST, s, launch_uncast(h->f32, out, cnt, s, &h->launches));
+  }
+  return AAO_OK;
+}
+
+// Preconditioned MINRES from x0 = (use_x0 ? x : 0) on Y T x = b; fills info.
+aao_status minres_core(aao_handle* h, const double* b, double* x, int use_x0, int nrhs, double rtol,
+                       int maxit, aao_solve_info* info, cudaStream_t s) {
+  const Plan& P = h->P;
+  const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
+  double* T = h->vT; double* v = h->vv; double* vp = h->vvp; double* z = h->vz;
+  double* zn = h->vzn; double* w = h->vw; double* wp = h->vwp;
+  double* p1 = h->partial;
+  double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
+  double* p3 = h->partial + (size_t)2 * h->nrhs_max * h->partial_stride;
+  int nb_yt = 0;
+  const int nb_dot = dot_blocks_per_rhs(P);
+  uint64_t* nl = &h->launches;
+
+  if (use_x0) {
+    AAO_KL(h, KC_YT, s, launch_yt(P, x, T, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
+    AAO_KL(h, KC_SUB, s, launch_sub(P, b, T, v, nrhs, s, nl));
+  } else {
+    AAO_CK(cudaMemsetAsync(x, 0, vb, s));
+    AAO_CK(cudaMemcpyAsync(v, b, vb, cudaMemcpyDeviceToDevice, s));
+  }
+  AAO_CK(cudaMemsetAsync(vp, 0, vb, s));
+  AAO_CK(cudaMemsetAsync(w, 0, vb, s));
+  AAO_CK(cudaMemsetAsync(wp, 0, vb, s));
+  AAO_TRY(prec_apply(h, v, z, nrhs, s));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, z, v, p1, nrhs, s, nl));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, b, b, p2, nrhs, s, nl));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, v, v, p3, nrhs, s, nl));
+  AAO_KL(h, KC_SCAL, s, launch_scalars(0, h->sc, p1, nb_dot, p2, nb_dot, p3, nb_dot, nrhs, rtol, maxit, s, nl));
+  const size_t scb = (size_t)nrhs * sizeof(MinresScalars);
+  AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
+  AAO_CK(cudaStreamSynchronize(s));
+  auto all_done = [&]() {
+    for (int r = 0; r < nrhs; ++r)
+      if (!h->sc_host[r].done) return false;
+    return true;
+  };
+  for (int it = 0; it < maxit && !all_done(); ++it) {
+    AAO_KL(h, KC_YT_DOT, s, launch_yt(P, z, T, z, p1, 1, nrhs, s, nl, &nb_yt));
+    AAO_KL(h, KC_SCAL, s, launch_scalars(1, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
+    AAO_KL(h, KC_VUPD, s, launch_vupdate(P, T, v, vp, h->sc, nrhs, s, nl));  // vp <- v_{j+1}
+    AAO_TRY(prec_apply(h, vp, zn, nrhs, s));
+    AAO_KL(h, KC_DOT, s, launch_dot(P, zn, vp, p1, nrhs, s, nl));
+    AAO_KL(h, KC_SCAL, s, launch_scalars(2, h->sc, p1, nb_dot, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
+    AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, z, wp, w, x, h->sc, nrhs, s, nl));  // wp <- w_{j+1}
+    AAO_KL(h, KC_YT_RES, s, launch_yt(P, x, nullptr, b, p1, 2, nrhs, s, nl, &nb_yt));
+    AAO_KL(h, KC_SCAL, s, launch_scalars(3, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
+    std::swap(v, vp);
+    std::swap(z, zn);
+    std::swap(w, wp);
+    AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
+    AAO_CK(cudaStreamSynchronize(s));
+  }
+  aao_status worst = AAO_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    const MinresScalars& S = h->sc_host[r];
+    aao_status st = (aao_status)S.status;
+    if (!S.done && st == AAO_OK) st = AAO_ENOTCONV;
+    if (info) {
+      info[r].iters = S.iters;
+      info[r].status = st;
+      info[r].relres_true = S.relres_true;
+      info[r].relres_est = S.relres_est;
+      info[r].ir_steps = 0;
+      info[r].reserved = 0;
+    }
+    if (st != AAO_OK && worst == AAO_OK) worst = st;
+  }
+  if (worst != AAO_OK) g_err = std::string("MINRES: ") + aao_status_str(worst);
+  return worst;
+}
+
+// Mixed precision: FP64 iterative refinement around MINRES with the FP32 preconditioner.
+aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int nrhs, double rtol,
+                    int maxit, aao_solve_info* info, cudaStream_t s) {
+  const Plan& P = h->P;
+  const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
+  const size_t cnt = (size_t)nrhs * h->vlen();
+  double* p1 = h->partial;
+  double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
+  uint64_t* nl = &h->launches;
+  if (!use_x0) AAO_CK(cudaMemsetAsync(x, 0, vb, s));
+  std::vector<aao_solve_info> inner(nrhs), acc(nrhs);
+  for (int r = 0; r < nrhs; ++r) { acc[r] = aao_solve_info{0, AAO_ENOTCONV, 1.0, 1.0, 0, 0}; }
+  // ||b||^2
+  const int nb_dot = dot_blocks_per_rhs(P);
+  AAO_KL(h, KC_DOT, s, launch_dot(P, b, b, p2, nrhs, s, nl));
+  std::vector<double> hp((size_t)nrhs * nb_dot);
+  AAO_CK(cudaMemcpyAsync(hp.data(), p2, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AAO_CK(cudaStreamSynchronize(s));
+  std::vector<double> bn(nrhs, 0.0);
+  for (int r = 0; r < nrhs; ++r) {
+    double t = 0;
+    for (int i = 0; i < nb_dot; ++i) t += hp[(size_t)r * nb_dot + i];
+    bn[r] = std::sqrt(t > 0 ? t : 1.0);
+  }
+  const int max_ir = 30;
+  int total_its = 0;
+  aao_status worst = AAO_ENOTCONV;
+  for (int ir = 0; ir < max_ir; ++ir) {
+    // r = b - Y T x (FP64), its norm
+    int nb_yt = 0;
+    AAO_KL(h, KC_YT, s, launch_yt(P, x, h->vT, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
+    AAO_KL(h, KC_SUB, s, launch_sub(P, b, h->vT, h->vr, nrhs, s, nl));
+    AAO_KL(h, KC_DOT, s, launch_dot(P, h->vr, h->vr, p1, nrhs, s, nl));
+    AAO_CK(cudaMemcpyAsync(hp.data(), p1, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AAO_CK(cudaStreamSynchronize(s));
+    bool all = true;
+    double worst_rel = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+      double t = 0;
+      for (int i = 0; i < nb_dot; ++i) t += hp[(size_t)r * nb_dot + i];
+      const double rel = std::sqrt(t) / bn[r];
+      acc[r].relres_true = rel;
+      acc[r].ir_steps = ir;
+      if (rel <= rtol) acc[r].status = AAO_OK; else all = false;
+      worst_rel = std::max(worst_rel, rel);
+    }
+    if (all) { worst = AAO_OK; break; }
+    if (total_its >= maxit) break;
+    // inner solve: Y T dx = r to a relative tolerance that reaches rtol overall
+    double inner_tol = std::max(rtol / worst_rel, 1e-6);
+    inner_tol = std::min(inner_tol, 1e-2);
+    aao_status st = minres_core(h, h->vr, h->vdx, 0, nrhs, inner_tol, maxit - total_its, inner.data(), s);
+    (void)st;
+    int its = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      its = std::max(its, inner[r].iters);
+      acc[r].iters += inner[r].iters;
+      acc[r].relres_est = inner[r].relres_est;
+    }
+    total_its += std::max(its, 1);
+    // x += dx, but only for the right-hand sides not yet converged
+    for (int r = 0; r < nrhs; ++r) {
+      if (acc[r].status == AAO_OK) continue;
+      AAO_KL(h, KC_AXPY, s, launch_axpy(1.0, h->vdx + (size_t)r * h->vlen(), x + (size_t)r * h->vlen(), h->vlen(), s, nl));
+    }
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    if (info) info[r] = acc[r];
+    if (acc[r].status != AAO_OK && worst == AAO_OK) worst = (aao_status)acc[r].status;
+  }
+  (void)cnt;
+  if (worst != AAO_OK) g_err = std::string("MINRES (FP32 preconditioner + FP64 refinement): ") + aao_status_str(worst);
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* aao_status_str(aao_status s) {
+  switch (s) {
+    case AAO_OK: return "AAO_OK";
+    case AAO_EINVAL: return "AAO_EINVAL";
+    case AAO_EUNSUPPORTED: return "AAO_EUNSUPPORTED";
+    case AAO_ENOMEM: return "AAO_ENOMEM";
+    case AAO_ECUDA: return "AAO_ECUDA";
+    case AAO_ENOTCONV: return "AAO_ENOTCONV";
+    case AAO_EBREAKDOWN: return "AAO_EBREAKDOWN";
+    case AAO_ESINGULAR: return "AAO_ESINGULAR";
+    case AAO_EBUSY: return "AAO_EBUSY";
+    case AAO_EPENDING: return "AAO_EPENDING";
+    case AAO_ETIMEOUT: return "AAO_ETIMEOUT";
+  }
+  return "AAO_UNKNOWN";
+}
+
+const char* aao_last_error(void) { return g_err.c_str(); }
+
+aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aao_scheme scheme,
+                      const aao_opts* opts, aao_handle** out) {
+  g_err.clear();
+  if (!grid || !out) return fail(AAO_EINVAL, "null grid or out pointer");
+  *out = nullptr;
+  if (grid->dim < 1 || grid->dim > 3) return fail(AAO_EINVAL, "dim must be 1, 2 or 3");
+  if (!(tau > 0.0) || !std::isfinite(tau)) return fail(AAO_EINVAL, "tau must be > 0");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return fail(AAO_EINVAL, "alpha must be in (0, 1]");
+  if (!(grid->c2 > 0.0) || !std::isfinite(grid->c2)) return fail(AAO_EINVAL, "c2 must be > 0");
+  if (scheme != AAO_SCHEME_IMPLICIT_LEAPFROG) return fail(AAO_EINVAL, "unknown scheme");
+  if (nt < 2) return fail(AAO_EINVAL, "nt must be >= 2");
+  const int M = grid->N + 1;
+  if (!is_pow2(M) || M < 64 || M > 512)
+    return fail(AAO_EUNSUPPORTED, "N+1 must be a power of two in [64, 512]");
+  if (!is_pow2(nt) || nt < 64 || nt > 1024)
+    return fail(AAO_EUNSUPPORTED, "nt must be a power of two in [64, 1024]");
+  aao_opts o{};
+  o.precision = AAO_PREC_FP64;
+  o.nrhs_max = 1;
+  if (opts) o = *opts;
+  if (o.nrhs_max < 1) o.nrhs_max = 1;
+  if (o.precision != AAO_PREC_FP64 && o.precision != AAO_PREC_FP32_IR)
+    return fail(AAO_EINVAL, "unknown precision");
+  for (int i = 0; i < 6; ++i)
+    if (o.reserved[i] != 0) return fail(AAO_EINVAL, "opts.reserved must be zero");
+
+  aao_handle* h = new aao_handle();
+  cudaGetDevice(&h->device);
+  h->precision = o.precision;
+  h->nrhs_max = o.nrhs_max;
+  Plan& P = h->P;
+  P.d = grid->dim;
+  P.N = grid->N;
+  P.M = M;
+  P.n = nt;
+  P.m = 1;
+  for (int i = 0; i < P.d; ++i) P.m *= P.N;
+  P.npairs = (P.m + 1) / 2;
+  P.tau = tau;
+  P.alpha = alpha;
+  P.c2 = grid->c2;
+  P.h = 1.0 / (double)M;
+  P.coef = P.c2 * tau * tau / (2.0 * P.h * P.h);
+
+  auto bail = [&](aao_status st) { delete h; return st; };
+
+  // ---- host tables (long double, rounded) ----
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<double2> twS, twT, wq(2 * (size_t)nt);
+  host_twiddles(M, -1, twS);
+  host_twiddles(nt, -1, twT);
+  std::vector<double> sinw(M / 2 + 1), dinv(nt), d2(nt), mu(P.N);
+  const long double cM = sqrtl(2.0L / (long double)M);
+  for (int j = 0; j <= M / 2; ++j) sinw[j] = (double)(cM * sinl(pi * j / (long double)M) / 2.0L);
+  const long double la = logl((long double)alpha);
+  {
+    // per-frequency terms of Sigma = (1 - a theta^k)^2 + (Lambda - 1)(1 + a^2 theta^{2k})
+    const long double a = expl(la / nt), one_minus_a = -expm1l(la / nt);
+    for (int k = 0; k < nt; ++k) {
+      const long double phi = 2.0L * pi * (long double)k / (long double)nt;
+      const long double sh = sinl(phi / 2.0L), c = cosl(phi), sn = sinl(phi);
+      const long double wr = one_minus_a + 2.0L * a * sh * sh, wi = -a * sn;
+      wq[2 * k] = make_double2((double)((wr - wi) * (wr + wi)), (double)(2.0L * wr * wi));
+      const long double qr = one_minus_a * (1.0L + a) + 2.0L * a * a * c * c;
+      wq[2 * k + 1] = make_double2((double)qr, (double)(2.0L * a * a * sn * c));
+    }
+  }
+  for (int t = 0; t < nt; ++t) {
+    dinv[t] = (double)expl(-la * (long double)t / (long double)nt);
+    d2[t] = (double)expl(2.0L * la * (long double)t / (long double)nt);
+  }
+  const long double hl = 1.0L / (long double)M;
+  for (int i = 0; i < P.N; ++i) {
+    const long double sv = sinl((long double)(i + 1) * pi * hl / 2.0L);
+    mu[i] = (double)(4.0L / (hl * hl) * sv * sv);
+  }
+
+  // ---- device allocations ----
+  aao_status st;
+  const size_t tabn = (size_t)(nt / 2 + 1) * P.npairs * 2;
+  double* d_mu = nullptr; double2* d_wq = nullptr; double* d_mm = nullptr;
+  if ((st = h->alloc(&h->tw_space64, M)) || (st = h->alloc(&h->sinw64, M / 2 + 1)) ||
+      (st = h->alloc(&h->tw_time64, nt)) || (st = h->alloc(&h->dinv64, nt)) ||
+      (st = h->alloc(&h->d264, nt)) || (st = h->alloc(&h->ab64, tabn)) ||
+      (st = h->alloc(&d_mu, P.N)) || (st = h->alloc(&d_wq, 2 * (size_t)nt)))
+    return bail(st);
+  const bool fp32 = (o.precision == AAO_PREC_FP32_IR);
+  if (fp32) {
+    if ((st = h->alloc(&h->tw_space32, M)) || (st = h->alloc(&h->sinw32, M / 2 + 1)) ||
+        (st = h->alloc(&h->tw_time32, nt)) || (st = h->alloc(&h->dinv32, nt)) ||
+        (st = h->alloc(&h->d232, nt)) || (st = h->alloc(&h->ab32, tabn)))
+      return bail(st);
+  }
+  const size_t vl = (size_t)h->nrhs_max * (size_t)nt * P.m;
+  if ((st = h->alloc(&h->vT, vl)) || (st = h->alloc(&h->vv, vl)) || (st = h->alloc(&h->vvp, vl)) ||
+      (st = h->alloc(&h->vz, vl)) || (st = h->alloc(&h->vzn, vl)) || (st = h->alloc(&h->vw, vl)) ||
+      (st = h->alloc(&h->vwp, vl)))
+    return bail(st);
+  if (fp32) {
+    if ((st = h->alloc(&h->vr, vl)) || (st = h->alloc(&h->vdx, vl)) || (st = h->alloc(&h->f32, vl)))
+      return bail(st);
+  }
+  h->partial_stride = std::max(yt_blocks_per_rhs(P), dot_blocks_per_rhs(P));
+  if ((st = h->alloc(&h->partial, (size_t)3 * h->nrhs_max * h->partial_stride)) ||
+      (st = h->alloc(&h->sc, (size_t)h->nrhs_max)))
+    return bail(st);
+  if (cudaMallocHost(&h->sc_host, sizeof(MinresScalars) * h->nrhs_max) != cudaSuccess) {
+    cudaGetLastError();
+    h->sc_host = nullptr;
+    return bail(fail(AAO_ENOMEM, "cudaMallocHost failed"));
+  }
+
+  auto run = [&]() -> aao_status {
+    AAO_TRY(upload(twS, h->tw_space64));
+    AAO_TRY(upload(sinw, h->sinw64));
+    AAO_TRY(upload(twT, h->tw_time64));
+    AAO_TRY(upload(dinv, h->dinv64));
+    AAO_TRY(upload(d2, h->d264));
+    AAO_TRY(upload(mu, d_mu));
+    AAO_TRY(upload(wq, d_wq));
+    if (fp32) {
+      AAO_TRY(upload(to_f2(twS), h->tw_space32));
+      AAO_TRY(upload(to_f(sinw), h->sinw32));
+      AAO_TRY(upload(to_f2(twT), h->tw_time32));
+      AAO_TRY(upload(to_f(dinv), h->dinv32));
+      AAO_TRY(upload(to_f(d2), h->d232));
+    }
+    P.t64.tw_space = h->tw_space64; P.t64.sinw = h->sinw64; P.t64.tw_time = h->tw_time64;
+    P.t64.dinv = h->dinv64; P.t64.d2 = h->d264; P.t64.ab = h->ab64;
+    P.t64.cq = (double)(cM / 4.0L);
+    if (fp32) {
+      P.t32.tw_space = h->tw_space32; P.t32.sinw = h->sinw32; P.t32.tw_time = h->tw_time32;
+      P.t32.dinv = h->dinv32; P.t32.d2 = h->d232; P.t32.ab = h->ab32;
+      P.t32.cq = (float)(cM / 4.0L);
+    }
+    const long long total = (long long)(nt / 2 + 1) * P.npairs;
+    const int nbk = (int)((total + 255) / 256);
+    AAO_TRY(h->alloc(&d_mm, (size_t)2 * nbk));
+    int nb = 0;
+    AAO_CK(launch_spectral_table(P, d_mu, d_wq, h->ab64, fp32 ? h->ab32 : nullptr, d_mm, &nb,
+                                 0, &h->launches));
+    std::vector<double> mm((size_t)2 * nb);
+    AAO_CK(cudaMemcpy(mm.data(), d_mm, mm.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    double smin = 1e300, smax = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      smin = std::min(smin, mm[2 * i]);
+      smax = std::max(smax, mm[2 * i + 1]);
+    }
+    if (!(smin > 1e-12 * smax))
+      return fail(AAO_ESINGULAR, "min |Sigma| / max |Sigma| = " + std::to_string(smin / smax) +
+                                     " below 1e-12: preconditioner singular");
+    AAO_CK(cudaDeviceSynchronize());
+    return AAO_OK;
+  };
+  st = run();
+  if (st != AAO_OK) return bail(st);
+  *out = h;
+  return AAO_OK;
+}
+
+aao_status aao_destroy(aao_handle* h) {
+  if (!h) return AAO_OK;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  delete h;
+  return AAO_OK;
+}
+
+size_t aao_workspace_bytes(const aao_handle* h) { return h ? h->bytes : 0; }
+
+uint64_t aao_launch_count(const aao_handle* h) { return h ? h->launches : 0; }
+
+aao_status aao_profile_enable(aao_handle* h, int on) {
+  if (!h) return fail(AAO_EINVAL, "null handle");
+  if (on) {
+    for (auto& r : h->prof) cudaEventSynchronize(r.b);
+    h->clear_prof();
+  }
+  h->prof_on = (on != 0);
+  return AAO_OK;
+}
+
+int aao_profile_read(aao_handle* h, aao_kernel_stat* out, int max) {
+  if (!h) { fail(AAO_EINVAL, "null handle"); return -1; }
+  uint64_t cnt[KC_N] = {0};
+  double ms[KC_N] = {0};
+  for (auto& r : h->prof) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) { fail(AAO_ECUDA, "event sync failed"); return -1; }
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { fail(AAO_ECUDA, "event time failed"); return -1; }
+    cnt[r.cls] += 1;
+    ms[r.cls] += t;
+  }
+  int n = 0;
+  for (int c = 0; c < KC_N; ++c) {
+    if (!cnt[c]) continue;
+    if (out && n < max) {
+      std::memset(out[n].name, 0, sizeof(out[n].name));
+      std::strncpy(out[n].name, kc_name(c), sizeof(out[n].name) - 1);
+      out[n].launches = cnt[c];
+      out[n].total_ms = ms[c];
+    }
+    ++n;
+  }
+  return n;
+}
+
+aao_status aao_build_rhs(aao_handle* h, const double* f, const double* psi0, const double* psi1,
+                         double* b, int nrhs, void* stream) {
+  AAO_TRY(check_call(h, nrhs));
+  if (!f || !psi0 || !psi1 || !b) return fail(AAO_EINVAL, "null pointer");
+  AAO_KL(h, KC_RHS, (cudaStream_t)stream, launch_build_rhs(h->P, f, psi0, psi1, b, nrhs, (cudaStream_t)stream, &h->launches));
+  return AAO_OK;
+}
+
+aao_status aao_apply_op(aao_handle* h, const double* x, double* y, int nrhs, void* stream) {
+  AAO_TRY(check_call(h, nrhs));
+  if (!x || !y) return fail(AAO_EINVAL, "null pointer");
+  if (x == y) return fail(AAO_EINVAL, "x and y must not alias");
+  AAO_KL(h, KC_YT, (cudaStream_t)stream, launch_yt(h->P, x, y, nullptr, nullptr, 0, nrhs, (cudaStream_t)stream, &h->launches, nullptr));
+  return AAO_OK;
+}
+
+aao_status aao_apply_prec(aao_handle* h, const double* r, double* z, int nrhs, void* stream) {
+  AAO_TRY(check_call(h, nrhs));
+  if (!r || !z) return fail(AAO_EINVAL, "null pointer");
+  return prec_apply(h, r, z, nrhs, (cudaStream_t)stream);
+}
+
+aao_status aao_apply_dst(aao_handle* h, const double* x, double* y, int nrhs, void* stream) {
+  AAO_TRY(check_call(h, nrhs));
+  if (!x || !y) return fail(AAO_EINVAL, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  AAO_KL(h, KC_DST_X64, s, launch_dst_axis<double>(h->P, x, y, 0, nrhs, s, &h->launches));
+  for (int ax = 1; ax < h->P.d; ++ax)
+    AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(h->P, y, y, ax, nrhs, s, &h->launches));
+  return AAO_OK;
+}
+
+aao_status aao_apply_time(aao_handle* h, const double* x, double* y, int nrhs, void* stream) {
+  AAO_TRY(check_call(h, nrhs));
+  if (!x || !y) return fail(AAO_EINVAL, "null pointer");
+  AAO_KL(h, KC_TIME64, (cudaStream_t)stream, launch_time<double>(h->P, x, y, nrhs, (cudaStream_t)stream, &h->launches));
+  return AAO_OK;
+}
+
+aao_status aao_minres_solve(aao_handle* h, const double* b, double* x, int use_x0, int nrhs,
+                            double rtol, int maxit, aao_solve_info* info, void* stream) {
+  AAO_TRY(check_call(h, nrhs));
+  if (!b || !x) return fail(AAO_EINVAL, "null pointer");
+  if (b == x) return fail(AAO_EINVAL, "b and x must not alias");
+  if (!(rtol >= 0.0) || maxit < 1) return fail(AAO_EINVAL, "rtol must be >= 0 and maxit >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->precision == AAO_PREC_FP32_IR) return solve_ir(h, b, x, use_x0, nrhs, rtol, maxit, info, s);
+  return minres_core(h, b, x, use_x0, nrhs, rtol, maxit, info, s);
+}
+
+aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, const double* psi1,
+                          double* u, int nrhs, double rtol, int maxit, aao_solve_info* info,
+                          void* stream) {
+  AAO_TRY(check_call(h, nrhs));
+  if (!f || !psi0 || !psi1 || !u) return fail(AAO_EINVAL, "null pointer");
+  const size_t vl = (size_t)h->nrhs_max * h->vlen();
+  if (!h->hs_f) {
+    AAO_TRY(h->alloc(&h->hs_f, vl));
+    AAO_TRY(h->alloc(&h->hs_b, vl));
+    AAO_TRY(h->alloc(&h->hs_x, vl));
+    AAO_TRY(h->alloc(&h->hs_psi, (size_t)2 * h->nrhs_max * h->P.m));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
+  const size_t pb = (size_t)nrhs * h->P.m * sizeof(double);
+  double* d_psi0 = h->hs_psi;
+  double* d_psi1 = h->hs_psi + (size_t)h->nrhs_max * h->P.m;
+  AAO_CK(cudaMemcpyAsync(h->hs_f, f, vb, cudaMemcpyHostToDevice, s));
+  AAO_CK(cudaMemcpyAsync(d_psi0, psi0, pb, cudaMemcpyHostToDevice, s));
+  AAO_CK(cudaMemcpyAsync(d_psi1, psi1, pb, cudaMemcpyHostToDevice, s));
+  AAO_KL(h, KC_RHS, s, launch_build_rhs(h->P, h->hs_f, d_psi0, d_psi1, h->hs_b, nrhs, s, &h->launches));
+  aao_status st = aao_minres_solve(h, h->hs_b, h->hs_x, 0, nrhs, rtol, maxit, info, stream);
+  if (st != AAO_OK && st != AAO_ENOTCONV && st != AAO_EBREAKDOWN) return st;
+  AAO_CK(cudaMemcpyAsync(u, h->hs_x, vb, cudaMemcpyDeviceToHost, s));
+  AAO_CK(cudaStreamSynchronize(s));
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal declarations shared by the CUDA translation units of libaao.so.
+//
+// Data layout (all FP64 vectors): time-major, (rhs, i, s) -> (rhs*n + i)*m + s,
+// s lexicographic with x fastest.  Spatial lines along axis a have stride N^a.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "aao.h"
+
+namespace aao {
+
+#define AAO_HD __host__ __device__ __forceinline__
+
+// ---------------------------------------------------------------------------
+// complex helpers (double2 / float2 = re, im)
+// ---------------------------------------------------------------------------
+AAO_HD double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+AAO_HD double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+AAO_HD double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+AAO_HD double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -(a.x * b.y)));
+}
+AAO_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+AAO_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+AAO_HD float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
+}
+AAO_HD float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -(a.x * b.y)));
+}
+
+template <typename R> struct Cplx;
+template <> struct Cplx<double> { using T = double2; };
+template <> struct Cplx<float> { using T = float2; };
+
+// ---------------------------------------------------------------------------
+// problem plan: sizes and device tables, built once by aao_create
+// ---------------------------------------------------------------------------
+template <typename R>
+struct PrecTables {
+  using C = typename Cplx<R>::T;
+  const C* tw_space = nullptr;  // M entries, exp(-2 pi i q / M)
+  const R* sinw = nullptr;      // M/2+1 entries, sqrt(2/M) sin(pi j / M) / 2
+  const C* tw_time = nullptr;   // n entries, exp(-2 pi i q / n)
+  const R* dinv = nullptr;      // n entries, alpha^{-t/n}
+  const R* d2 = nullptr;        // n entries, alpha^{2t/n}
+  const C* ab = nullptr;        // (n/2+1) * npairs * 2 entries: A_k, B_k per mode pair
+  R cq = 0;                     // sqrt(2/M) / 4
+};
+
+struct Plan {
+  int d = 0, N = 0, M = 0, n = 0, m = 0, npairs = 0;
+  double tau = 0, alpha = 0, c2 = 0, h = 0;
+  double coef = 0;  // c2 tau^2 / (2 h^2): L w = w - coef * (sum of neighbour differences)
+  PrecTables<double> t64;
+  PrecTables<float> t32;
+};
+
+template <typename R> inline const PrecTables<R>& tables(const Plan& P);
+template <> inline const PrecTables<double>& tables<double>(const Plan& P) { return P.t64; }
+template <> inline const PrecTables<float>& tables<float>(const Plan& P) { return P.t32; }
+
+// ---------------------------------------------------------------------------
+// launchers (each returns the CUDA error of its launch and counts launches)
+// ---------------------------------------------------------------------------
+// Spatial DST-I along axis `axis` (0 = x) for nrhs*n time levels, in -> out (may alias).
+template <typename R>
+cudaError_t launch_dst_axis(const Plan& P, const R* in, R* out, int axis, int nrhs,
+                            cudaStream_t s, uint64_t* nl);
+// Time pipeline (all spatial modes), in -> out (may alias).
+template <typename R>
+cudaError_t launch_time(const Plan& P, const R* in, R* out, int nrhs, cudaStream_t s, uint64_t* nl);
+
+// Stencil kernels.  mode 0: y = Y T x.  mode 1: y = Y T x and partial[b] = sum y*w.
+// mode 2: no y; partial[b] = sum (w - Y T x)^2  (w = b, the true residual).
+// Partials are laid out [rhs][blocks_per_rhs]; returns blocks per rhs in *nb.
+cudaError_t launch_yt(const Plan& P, const double* x, double* y, const double* w, double* partial,
+                      int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
+int yt_blocks_per_rhs(const Plan& P);
+
+cudaError_t launch_build_rhs(const Plan& P, const double* f, const double* psi0, const double* psi1,
+                             double* b, int nrhs, cudaStream_t s, uint64_t* nl);
+
+// Spectral factor table (device), returns min/max |Sigma| per block in mm (host-readable after sync).
+// wq: 2n entries, wq[2k] = (1 - a theta^k)^2, wq[2k+1] = 1 + a^2 theta^{2k}.
+cudaError_t launch_spectral_table(const Plan& P, const double* mu1d, const double2* wq,
+                                  double2* ab64, float2* ab32, double* mm, int* nblocks,
+                                  cudaStream_t s, uint64_t* nl);
+
+// MINRES helpers -----------------------------------------------------------
+struct MinresScalars {
+  double gam, gam_prev, gam1, eta, c, c_prev, s, s_prev, delta;
+  double bnorm2, relres_true, relres_est;
+  double cv[3];  // v_{j+1} = cv0*T + cv1*v_j + cv2*v_{j-1}
+  double cw[4];  // w_{j+1} = cw0*z_j + cw1*w_{j-1} + cw2*w_j ; x += cw3*w_{j+1}
+  double rtol;
+  int iters, maxit, done, status;
+};
+
+int dot_blocks_per_rhs(const Plan& P);
+// partial[rhs*nb + b] = sum_i a_i*c_i over the rhs's n*m entries
+cudaError_t launch_dot(const Plan& P, const double* a, const double* c, double* partial, int nrhs,
+                       cudaStream_t s, uint64_t* nl);
+// y = a0*x0 + a1*x1 + a2*x2 with coefficients sc[rhs].cv (which = 0) ; x2 may be null
+cudaError_t launch_vupdate(const Plan& P, const double* T, const double* v, double* vprev_out,
+                           const MinresScalars* sc, int nrhs, cudaStream_t s, uint64_t* nl);
+cudaError_t launch_wxupdate(const Plan& P, const double* z, double* wprev_out, const double* w,
+                            double* x, const MinresScalars* sc, int nrhs, cudaStream_t s,
+                            uint64_t* nl);
+// y = x0 - x1 (used for r0 = b - A x0)
+cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* y, int nrhs,
+                       cudaStream_t s, uint64_t* nl);
+// scalar steps: 0 = init (after z1, partial = <z1,v1>, partial2 = <b,b>, partial3 = <v1,v1>),
+// 1 = delta (partial = <Az, z>), 2 = gamma + Givens (partial = <z_{j+1}, v_{j+1}>),
+// 3 = true residual check (partial = sum r^2)
+cudaError_t launch_scalars(int step, MinresScalars* sc, const double* partial, int nb,
+                           const double* partial2, int nb2, const double* partial3, int nb3,
+                           int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl);
+cudaError_t launch_cast(const double* in, float* out, size_t count, cudaStream_t s, uint64_t* nl);
+cudaError_t launch_uncast(const float* in, double* out, size_t count, cudaStream_t s, uint64_t* nl);
+cudaError_t launch_axpy(double a, const double* x, double* y, size_t count, cudaStream_t s,
+                        uint64_t* nl);
+
+}  // namespace aao

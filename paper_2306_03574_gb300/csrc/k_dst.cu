@@ -1,0 +1,221 @@
+// Orthonormal DST-I along one spatial axis (the matrix S = U-factor of Section 2.3:
+// on a uniform grid the eigenvectors of L are the discrete sine transform).
+//
+// Two lines a, b of length N = M-1 are transformed by one complex FFT of length
+// M = N+1.  For one real line x_1..x_N (x_0 = x_M = 0) put
+//     y_j = sin(pi j/M)(x_j + x_{M-j}) + (x_j - x_{M-j})/2,   j = 0..M-1,
+// and let Y_k = sum_j y_j exp(-2 pi i jk/M).  Then the DST-I
+// X_k = sum_j x_j sin(pi jk/M) satisfies
+//     X_{2k}   = -Im Y_k,
+//     X_{2k+1} = X_{2k-1} + Re Y_k,   X_1 = Re Y_0 / 2,
+// (the symmetric part of y feeds the cosine sums, the antisymmetric part the
+// sine sums).  Lines a and b are packed as y^a + i y^b and separated after the
+// FFT through Y^a_k = (C_k + conj C_{M-k})/2, Y^b_k = (C_k - conj C_{M-k})/(2i).
+// The factor sqrt(2/M) and the 1/2 of the separation are folded into the
+// pre-processing weights.  The odd outputs are a prefix sum over k, done per
+// thread block of k and then across the threads of a line pair by shuffles.
+#include "aao_internal.cuh"
+#include "fft_smem.cuh"
+
+namespace aao {
+
+struct DstArgs {
+  int N;            // line length
+  long long nlines; // contiguous axis: number of lines (all rhs and time levels)
+  int st;           // strided axis: stride = extent of the contiguous inner index
+  long long nouter; // strided axis: number of outer blocks
+};
+
+template <typename R, int M, int NS, int NT, bool STRIDED>
+__global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, PrecTables<R> tb) {
+  using C = typename Cplx<R>::T;
+  constexpr int H = M / 2;
+  constexpr int TPS = NT / NS;     // threads per line pair in the post-processing
+  constexpr int KQ = H / TPS;      // k values per thread
+  static_assert(NT % NS == 0 && H % TPS == 0 && TPS <= 32 && (32 % TPS) == 0, "dst config");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* cbuf = reinterpret_cast<C*>(smem_raw);
+  C* tw = cbuf + NS * M;
+  R* sw = reinterpret_cast<R*>(tw + M);
+
+  const int tid = threadIdx.x;
+  const int N = a.N;
+  for (int i = tid; i < M; i += NT) tw[i] = tb.tw_space[i];
+  for (int i = tid; i <= H; i += NT) sw[i] = tb.sinw[i];
+
+  // line addressing
+  long long line0 = 0, obase = 0;
+  int i0 = 0;
+  if (!STRIDED) {
+    line0 = (long long)blockIdx.x * (2 * NS);
+  } else {
+    obase = (long long)blockIdx.x * ((long long)a.st * N);
+    i0 = blockIdx.y * (2 * NS);
+  }
+  __syncthreads();
+
+  // ---- pre-processing: y'_j, y'_{M-j} for j = 1..M/2 of lines a, b ----
+  const R cq = tb.cq;
+  for (int task = tid; task < NS * H; task += NT) {
+    int q, j;
+    if (!STRIDED) { q = task / H; j = task % H + 1; }
+    else { q = task % NS; j = task / NS + 1; }
+    R xa0 = 0, xa1 = 0, xb0 = 0, xb1 = 0;  // x_j, x_{M-j} of lines a, b
+    if (!STRIDED) {
+      const long long la = line0 + 2 * q;
+      if (la < a.nlines) {
+        const R* p = in + la * N;
+        xa0 = p[j - 1];
+        xa1 = p[M - j - 1];
+      }
+      if (la + 1 < a.nlines) {
+        const R* p = in + (la + 1) * N;
+        xb0 = p[j - 1];
+        xb1 = p[M - j - 1];
+      }
+    } else {
+      const int ia = i0 + 2 * q;
+      const R* p = in + obase + ia;
+      if (ia < a.st) {
+        xa0 = p[(long long)(j - 1) * a.st];
+        xa1 = p[(long long)(M - j - 1) * a.st];
+      }
+      if (ia + 1 < a.st) {
+        xb0 = p[(long long)(j - 1) * a.st + 1];
+        xb1 = p[(long long)(M - j - 1) * a.st + 1];
+      }
+    }
+    const R w = sw[j];
+    const R sa = xa0 + xa1, ta = cq * (xa0 - xa1);
+    const R sb = xb0 + xb1, tbb = cq * (xb0 - xb1);
+    C lo, hi;
+    lo.x = fma(w, sa, ta);  lo.y = fma(w, sb, tbb);
+    hi.x = fma(w, sa, -ta); hi.y = fma(w, sb, -tbb);
+    cbuf[q * M + j] = lo;
+    if (j != H) cbuf[q * M + M - j] = hi;
+  }
+  for (int q = tid; q < NS; q += NT) { C z; z.x = 0; z.y = 0; cbuf[q * M] = z; }
+  __syncthreads();
+
+  fft_block<M, NS, NT, false>(cbuf, tw);
+
+  // ---- post-processing: separate the two lines, prefix sum for odd outputs ----
+  const int q = tid / TPS, lq = tid % TPS;
+  const int k0 = lq * KQ;
+  R pa[KQ], pb[KQ], ia[KQ], ib[KQ];
+  {
+    R acc_a = 0, acc_b = 0;
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) {
+      const int k = k0 + i;
+      const C ck = cbuf[q * M + k];
+      R ra, rb;
+      if (k == 0) {
+        ra = ck.x; rb = ck.y; ia[i] = 0; ib[i] = 0;
+      } else {
+        const C cm = cbuf[q * M + M - k];
+        ra = ck.x + cm.x; rb = ck.y + cm.y;
+        ia[i] = cm.y - ck.y; ib[i] = ck.x - cm.x;
+      }
+      acc_a += ra; acc_b += rb;
+      pa[i] = acc_a; pb[i] = acc_b;
+    }
+  }
+  // exclusive scan of the per-thread totals across the TPS threads of line pair q
+  R inc_a = pa[KQ - 1], inc_b = pb[KQ - 1];
+#pragma unroll
+  for (int off = 1; off < TPS; off <<= 1) {
+    const R ua = __shfl_up_sync(0xffffffffu, inc_a, off, TPS);
+    const R ub = __shfl_up_sync(0xffffffffu, inc_b, off, TPS);
+    if (lq >= off) { inc_a += ua; inc_b += ub; }
+  }
+  R ex_a = __shfl_up_sync(0xffffffffu, inc_a, 1, TPS);
+  R ex_b = __shfl_up_sync(0xffffffffu, inc_b, 1, TPS);
+  if (lq == 0) { ex_a = 0; ex_b = 0; }
+  __syncthreads();  // all reads of the spectrum are done
+#pragma unroll
+  for (int i = 0; i < KQ; ++i) {
+    const int k = k0 + i;
+    C odd; odd.x = pa[i] + ex_a; odd.y = pb[i] + ex_b;
+    cbuf[q * M + 2 * k] = odd;            // X_{2k+1} -> index 2k
+    if (k >= 1) {
+      C ev; ev.x = ia[i]; ev.y = ib[i];
+      cbuf[q * M + 2 * k - 1] = ev;       // X_{2k}   -> index 2k-1
+    }
+  }
+  __syncthreads();
+
+  // ---- store ----
+  if (!STRIDED) {
+    const long long e0 = line0 * N;
+    const long long etot = a.nlines * (long long)N;
+    for (int e = tid; e < 2 * NS * N; e += NT) {
+      if (e0 + e >= etot) break;
+      const int l = e / N, j = e % N;
+      const C v = cbuf[(l >> 1) * M + j];
+      out[e0 + e] = (l & 1) ? v.y : v.x;
+    }
+  } else {
+    for (int task = tid; task < 2 * NS * N; task += NT) {
+      const int l = task % (2 * NS), j = task / (2 * NS);
+      const int il = i0 + l;
+      if (il < a.st) {
+        const C v = cbuf[(l >> 1) * M + j];
+        out[obase + (long long)j * a.st + il] = (l & 1) ? v.y : v.x;
+      }
+    }
+  }
+}
+
+template <typename R, int M>
+static cudaError_t dst_launch_M(const Plan& P, const R* in, R* out, int axis, int nrhs,
+                                cudaStream_t s) {
+  using C = typename Cplx<R>::T;
+  constexpr int NT = 128;
+  constexpr int NS = 2048 / M;
+  const PrecTables<R>& tb = tables<R>(P);
+  const size_t smem = sizeof(C) * (NS * M + M) + sizeof(R) * (M / 2 + 1);
+  DstArgs a;
+  a.N = P.N;
+  long long stride = 1;
+  for (int i = 0; i < axis; ++i) stride *= P.N;
+  const long long total = (long long)nrhs * P.n * P.m;
+  if (axis == 0) {
+    a.nlines = total / P.N;
+    a.st = 1;
+    a.nouter = 0;
+    auto kern = k_dst<R, M, NS, NT, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const long long nb = (a.nlines + 2 * NS - 1) / (2 * NS);
+    kern<<<dim3((unsigned)nb), NT, smem, s>>>(in, out, a, tb);
+  } else {
+    a.st = (int)stride;
+    a.nouter = total / (stride * P.N);
+    a.nlines = 0;
+    auto kern = k_dst<R, M, NS, NT, true>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int ntile = (int)((stride + 2 * NS - 1) / (2 * NS));
+    kern<<<dim3((unsigned)a.nouter, (unsigned)ntile), NT, smem, s>>>(in, out, a, tb);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_dst_axis(const Plan& P, const R* in, R* out, int axis, int nrhs,
+                            cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  switch (P.M) {
+    case 64: return dst_launch_M<R, 64>(P, in, out, axis, nrhs, s);
+    case 128: return dst_launch_M<R, 128>(P, in, out, axis, nrhs, s);
+    case 256: return dst_launch_M<R, 256>(P, in, out, axis, nrhs, s);
+    case 512: return dst_launch_M<R, 512>(P, in, out, axis, nrhs, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_dst_axis<double>(const Plan&, const double*, double*, int, int,
+                                             cudaStream_t, uint64_t*);
+template cudaError_t launch_dst_axis<float>(const Plan&, const float*, float*, int, int,
+                                            cudaStream_t, uint64_t*);
+
+}  // namespace aao

@@ -1,0 +1,276 @@
+// Preconditioned MINRES vector kernels and scalar recurrences on the device
+// (Section 3 uses MINRES with P_alpha; the recurrences are the standard
+// Lanczos + Givens form of preconditioned MINRES: with P = L L^T it is MINRES on
+// L^{-1} A L^{-T} written so that only P^{-1} is applied).
+//
+// Per iteration j (z~_j = P^{-1} v_j unnormalised, gamma_j = sqrt(<z~_j, v_j>)):
+//   delta_j  = <A z~_j, z~_j> / gamma_j^2
+//   v_{j+1}  = A z~_j / gamma_j - (delta_j/gamma_j) v_j - (gamma_j/gamma_{j-1}) v_{j-1}
+//   z~_{j+1} = P^{-1} v_{j+1},  gamma_{j+1} = sqrt(<z~_{j+1}, v_{j+1}>)
+//   a0 = c_j delta_j - c_{j-1} s_j gamma_j,  a1 = sqrt(a0^2 + gamma_{j+1}^2),
+//   a2 = s_j delta_j + c_{j-1} c_j gamma_j,  a3 = s_{j-1} gamma_j,
+//   c_{j+1} = a0/a1, s_{j+1} = gamma_{j+1}/a1,
+//   w_{j+1} = (z~_j/gamma_j - a3 w_{j-1} - a2 w_j)/a1,  x += c_{j+1} eta w_{j+1},  eta <- -s_{j+1} eta.
+// Every reduction is two-level and deterministic: fixed blocks write partial
+// sums, one warp per right-hand side adds them in a fixed order.
+#include "aao_internal.cuh"
+
+namespace aao {
+
+namespace {
+constexpr int VNT = 256;
+constexpr int DOT_BLOCKS = 296;  // partial sums per right-hand side (2 per SM)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(VNT) k_dot(const double* __restrict__ a, const double* __restrict__ c,
+                                             double* __restrict__ partial, long long len) {
+  const long long rb = (long long)blockIdx.y * len;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT)
+    acc = fma(a[rb + i], c[rb + i], acc);
+  __shared__ double red[VNT / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < VNT / 32) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(VNT) k_vupdate(const double* __restrict__ T, const double* __restrict__ v,
+                                                 double* vprev, const MinresScalars* __restrict__ sc,
+                                                 long long len) {
+  const MinresScalars& S = sc[blockIdx.y];
+  const long long rb = (long long)blockIdx.y * len;
+  const bool dn = S.done != 0;
+  const double c0 = S.cv[0], c1 = S.cv[1], c2 = S.cv[2];
+  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT) {
+    const long long k = rb + i;
+    vprev[k] = dn ? 0.0 : fma(c0, T[k], fma(c1, v[k], c2 * vprev[k]));
+  }
+}
+
+__global__ void __launch_bounds__(VNT) k_wxupdate(const double* __restrict__ z, double* wprev,
+                                                  const double* __restrict__ w, double* __restrict__ x,
+                                                  const MinresScalars* __restrict__ sc, long long len) {
+  const MinresScalars& S = sc[blockIdx.y];
+  if (S.done) return;
+  const long long rb = (long long)blockIdx.y * len;
+  const double c0 = S.cw[0], c1 = S.cw[1], c2 = S.cw[2], c3 = S.cw[3];
+  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT) {
+    const long long k = rb + i;
+    const double wn = fma(c0, z[k], fma(c1, wprev[k], c2 * w[k]));
+    wprev[k] = wn;
+    x[k] = fma(c3, wn, x[k]);
+  }
+}
+
+__global__ void __launch_bounds__(VNT) k_sub(const double* __restrict__ a, const double* __restrict__ b,
+                                             double* __restrict__ y, long long len) {
+  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT)
+    y[i] = a[i] - b[i];
+}
+
+__global__ void __launch_bounds__(VNT) k_cast(const double* __restrict__ in, float* __restrict__ out,
+                                              long long len) {
+  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT)
+    out[i] = (float)in[i];
+}
+
+__global__ void __launch_bounds__(VNT) k_uncast(const float* __restrict__ in, double* __restrict__ out,
+                                                long long len) {
+  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT)
+    out[i] = (double)in[i];
+}
+
+__global__ void __launch_bounds__(VNT) k_axpy(double a, const double* __restrict__ x,
+                                              double* __restrict__ y, long long len) {
+  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+// deterministic sum of nb partials of right-hand side r by one warp
+__device__ __forceinline__ double sum_partials(const double* p, int nb) {
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) t += p[i];
+  return warp_sum(t);
+}
+
+__global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict__ p1, int nb1,
+                          const double* __restrict__ p2, int nb2, const double* __restrict__ p3,
+                          int nb3, double rtol, int maxit) {
+  const int r = blockIdx.x;
+  MinresScalars& S = sc[r];
+  const double s1 = sum_partials(p1 + (long long)r * nb1, nb1);
+  double s2 = 0.0, s3 = 0.0;
+  if (step == 0) {
+    s2 = sum_partials(p2 + (long long)r * nb2, nb2);
+    s3 = sum_partials(p3 + (long long)r * nb3, nb3);
+  }
+  if (threadIdx.x != 0) return;
+  if (step == 0) {
+    // s1 = <z1, v1>, s2 = <b, b>, s3 = <v1, v1>
+    S.rtol = rtol;
+    S.maxit = maxit;
+    S.iters = 0;
+    S.status = AAO_OK;
+    S.done = 0;
+    S.bnorm2 = (s2 > 0.0) ? s2 : 1.0;
+    S.relres_true = sqrt(s3 / S.bnorm2);
+    S.relres_est = 1.0;
+    S.gam_prev = 1.0;
+    S.c = S.c_prev = 1.0;
+    S.s = S.s_prev = 0.0;
+    S.delta = 0.0;
+    for (int i = 0; i < 3; ++i) S.cv[i] = 0.0;
+    for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
+    if (s1 < 0.0) { S.status = AAO_EBREAKDOWN; S.done = 1; }
+    if (s1 == 0.0 || S.relres_true <= rtol) S.done = 1;
+    S.gam = S.done ? 0.0 : sqrt(s1);
+    S.gam1 = S.gam;
+    S.eta = S.gam;
+    return;
+  }
+  if (S.done) {
+    for (int i = 0; i < 3; ++i) S.cv[i] = 0.0;
+    for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
+    return;
+  }
+  if (step == 1) {
+    const double g = S.gam;
+    S.delta = s1 / (g * g);
+    S.cv[0] = 1.0 / g;
+    S.cv[1] = -S.delta / g;
+    S.cv[2] = -g / S.gam_prev;
+  } else if (step == 2) {
+    if (s1 < 0.0) {
+      S.status = AAO_EBREAKDOWN;
+      S.done = 1;
+      for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
+      return;
+    }
+    const double gn = sqrt(s1);
+    const double g = S.gam, dl = S.delta;
+    const double a0 = S.c * dl - S.c_prev * S.s * g;
+    const double a1 = sqrt(a0 * a0 + gn * gn);
+    const double a2 = S.s * dl + S.c_prev * S.c * g;
+    const double a3 = S.s_prev * g;
+    if (a1 == 0.0) {
+      S.status = AAO_EBREAKDOWN;
+      S.done = 1;
+      for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
+      return;
+    }
+    const double cn = a0 / a1, sn = gn / a1;
+    S.cw[0] = 1.0 / (g * a1);
+    S.cw[1] = -a3 / a1;
+    S.cw[2] = -a2 / a1;
+    S.cw[3] = cn * S.eta;
+    S.eta = -sn * S.eta;
+    S.gam_prev = g;
+    S.gam = gn;
+    S.c_prev = S.c;
+    S.c = cn;
+    S.s_prev = S.s;
+    S.s = sn;
+    S.iters += 1;
+    S.relres_est = fabs(S.eta) / S.gam1;
+  } else if (step == 3) {
+    S.relres_true = sqrt(s1 / S.bnorm2);
+    if (S.relres_true <= S.rtol) {
+      S.done = 1;
+      S.status = AAO_OK;
+    } else if (S.iters >= S.maxit || S.gam == 0.0) {
+      S.done = 1;
+      S.status = AAO_ENOTCONV;
+    }
+  }
+}
+
+inline dim3 vgrid(const Plan& P, int nrhs) {
+  const long long len = (long long)P.n * P.m;
+  long long b = (len + VNT - 1) / VNT;
+  if (b > 152 * 8) b = 152 * 8;
+  return dim3((unsigned)b, nrhs);
+}
+
+}  // namespace
+
+int dot_blocks_per_rhs(const Plan&) { return DOT_BLOCKS; }
+
+cudaError_t launch_dot(const Plan& P, const double* a, const double* c, double* partial, int nrhs,
+                       cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  k_dot<<<dim3(DOT_BLOCKS, nrhs), VNT, 0, s>>>(a, c, partial, (long long)P.n * P.m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vupdate(const Plan& P, const double* T, const double* v, double* vprev_out,
+                           const MinresScalars* sc, int nrhs, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  k_vupdate<<<vgrid(P, nrhs), VNT, 0, s>>>(T, v, vprev_out, sc, (long long)P.n * P.m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wxupdate(const Plan& P, const double* z, double* wprev_out, const double* w,
+                            double* x, const MinresScalars* sc, int nrhs, cudaStream_t s,
+                            uint64_t* nl) {
+  if (nl) ++*nl;
+  k_wxupdate<<<vgrid(P, nrhs), VNT, 0, s>>>(z, wprev_out, w, x, sc, (long long)P.n * P.m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* y, int nrhs,
+                       cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  const long long len = (long long)nrhs * P.n * P.m;
+  long long nb = (len + VNT - 1) / VNT;
+  if (nb > 152 * 8) nb = 152 * 8;
+  k_sub<<<(unsigned)nb, VNT, 0, s>>>(a, b, y, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast(const double* in, float* out, size_t count, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  long long nb = ((long long)count + VNT - 1) / VNT;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  k_cast<<<(unsigned)nb, VNT, 0, s>>>(in, out, (long long)count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_uncast(const float* in, double* out, size_t count, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  long long nb = ((long long)count + VNT - 1) / VNT;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  k_uncast<<<(unsigned)nb, VNT, 0, s>>>(in, out, (long long)count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(double a, const double* x, double* y, size_t count, cudaStream_t s,
+                        uint64_t* nl) {
+  if (nl) ++*nl;
+  long long nb = ((long long)count + VNT - 1) / VNT;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  k_axpy<<<(unsigned)nb, VNT, 0, s>>>(a, x, y, (long long)count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalars(int step, MinresScalars* sc, const double* partial, int nb,
+                           const double* partial2, int nb2, const double* partial3, int nb3,
+                           int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  k_scalars<<<nrhs, 32, 0, s>>>(step, sc, partial, nb, partial2, nb2, partial3, nb3, rtol, maxit);
+  return cudaGetLastError();
+}
+
+}  // namespace aao

@@ -1,0 +1,176 @@
+// Y T v as a stencil x time-band kernel (Section 2.3, first paragraph: T is
+// sparse, Y only reverses the time levels), and the right-hand side b = Y f of
+// eq. (main_matrix).
+//
+// (T v)_i = L v_i - 2 v_{i-1} + L v_{i-2}, v_{-1} = v_{-2} = 0, L = I - coef*(-h^2 Delta_h),
+// L w(s) = (1 + 2d coef) w(s) - coef * sum_{neighbours s'} w(s'), Dirichlet zeros outside.
+// One thread owns one spatial point s and a run of CH time levels; it keeps
+// L v_{i-1}, L v_{i-2} and v_{i-1} in registers (two extra halo levels at the
+// start of its run) and writes (Y T v) at time slot n-1-i.  Optional fused
+// reductions: sum (YTv)*w  (the MINRES delta), or sum (w - YTv)^2 (the true
+// residual, with w = b).
+#include "aao_internal.cuh"
+
+namespace aao {
+
+namespace {
+
+constexpr int YT_NT = 256;
+constexpr int YT_CH = 32;
+
+struct YtArgs {
+  int N, n, m;
+  double coef, diag;
+};
+
+template <int D>
+__device__ __forceinline__ double apply_L(const double* __restrict__ v, int s, int ix, int iy, int iz,
+                                          const YtArgs& a) {
+  const int N = a.N;
+  double sum = (ix > 0 ? v[s - 1] : 0.0) + (ix < N - 1 ? v[s + 1] : 0.0);
+  if (D >= 2) sum += (iy > 0 ? v[s - N] : 0.0) + (iy < N - 1 ? v[s + N] : 0.0);
+  if (D >= 3) sum += (iz > 0 ? v[s - N * N] : 0.0) + (iz < N - 1 ? v[s + N * N] : 0.0);
+  return fma(-a.coef, sum, a.diag * v[s]);
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[YT_NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (l < YT_NT / 32) ? red[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(YT_NT) k_yt(const double* __restrict__ x, double* __restrict__ y,
+                                              const double* __restrict__ w,
+                                              double* __restrict__ partial, YtArgs a) {
+  const int s = blockIdx.x * YT_NT + threadIdx.x;
+  const int n = a.n, m = a.m, N = a.N;
+  const int i0 = blockIdx.y * YT_CH;
+  const int i1 = min(n, i0 + YT_CH);
+  const long long rb = (long long)blockIdx.z * n * m;
+  double acc = 0.0;
+  if (s < m) {
+    const int ix = s % N;
+    const int iy = (D >= 2) ? (s / N) % N : 0;
+    const int iz = (D >= 3) ? s / (N * N) : 0;
+    const double* xr = x + rb;
+    double Lv1 = 0.0, Lv2 = 0.0, v1 = 0.0;  // L v_{i-1}, L v_{i-2}, v_{i-1}
+    for (int i = max(0, i0 - 2); i < i1; ++i) {
+      const double* vi = xr + (long long)i * m;
+      const double Lv = apply_L<D>(vi, s, ix, iy, iz, a);
+      if (i >= i0) {
+        const double o = fma(-2.0, v1, Lv + Lv2);
+        const long long idx = rb + (long long)(n - 1 - i) * m + s;
+        if (MODE != 2) y[idx] = o;
+        if (MODE == 1) acc = fma(o, w[idx], acc);
+        if (MODE == 2) {
+          const double r = w[idx] - o;
+          acc = fma(r, r, acc);
+        }
+      }
+      Lv2 = Lv1;
+      Lv1 = Lv;
+      v1 = vi[s];
+    }
+  }
+  if (MODE != 0) {
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) {
+      const long long nb = (long long)gridDim.x * gridDim.y;
+      partial[blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// b[n-1-k] = tau^2 f^k for k >= 2; tau^2 f^1 - L psi0; tau^2 f^0/2 + tau psi1 + psi0.
+template <int D>
+__global__ void __launch_bounds__(YT_NT) k_rhs(const double* __restrict__ f,
+                                               const double* __restrict__ psi0,
+                                               const double* __restrict__ psi1,
+                                               double* __restrict__ b, YtArgs a, double tau) {
+  const int s = blockIdx.x * YT_NT + threadIdx.x;
+  const int k = blockIdx.y;
+  const int n = a.n, m = a.m, N = a.N;
+  if (s >= m) return;
+  const long long rb = (long long)blockIdx.z * n * m;
+  const long long ib = (long long)blockIdx.z * m;
+  const double t2 = tau * tau;
+  const double fk = f[rb + (long long)k * m + s];
+  double v;
+  if (k == 0) {
+    v = fma(0.5 * t2, fk, fma(tau, psi1[ib + s], psi0[ib + s]));
+  } else if (k == 1) {
+    const int ix = s % N;
+    const int iy = (D >= 2) ? (s / N) % N : 0;
+    const int iz = (D >= 3) ? s / (N * N) : 0;
+    v = fma(t2, fk, -apply_L<D>(psi0 + ib, s, ix, iy, iz, a));
+  } else {
+    v = t2 * fk;
+  }
+  b[rb + (long long)(n - 1 - k) * m + s] = v;
+}
+
+YtArgs make_args(const Plan& P) {
+  YtArgs a;
+  a.N = P.N;
+  a.n = P.n;
+  a.m = P.m;
+  a.coef = P.coef;
+  a.diag = 1.0 + 2.0 * P.d * P.coef;
+  return a;
+}
+
+}  // namespace
+
+int yt_blocks_per_rhs(const Plan& P) {
+  return ((P.m + YT_NT - 1) / YT_NT) * ((P.n + YT_CH - 1) / YT_CH);
+}
+
+template <int D>
+static void yt_dispatch(int mode, dim3 g, cudaStream_t s, const double* x, double* y,
+                        const double* w, double* partial, const YtArgs& a) {
+  if (mode == 0) k_yt<D, 0><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
+  else if (mode == 1) k_yt<D, 1><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
+  else k_yt<D, 2><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
+}
+
+cudaError_t launch_yt(const Plan& P, const double* x, double* y, const double* w, double* partial,
+                      int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb) {
+  if (nl) ++*nl;
+  const YtArgs a = make_args(P);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
+  if (nb) *nb = (int)(g.x * g.y);
+  switch (P.d) {
+    case 1: yt_dispatch<1>(mode, g, s, x, y, w, partial, a); break;
+    case 2: yt_dispatch<2>(mode, g, s, x, y, w, partial, a); break;
+    case 3: yt_dispatch<3>(mode, g, s, x, y, w, partial, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_rhs(const Plan& P, const double* f, const double* psi0, const double* psi1,
+                             double* b, int nrhs, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  const YtArgs a = make_args(P);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, P.n, nrhs);
+  switch (P.d) {
+    case 1: k_rhs<1><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
+    case 2: k_rhs<2><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
+    case 3: k_rhs<3><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace aao

@@ -1,0 +1,158 @@
+// Time part of P_alpha^{-1} for every spatial mode j (Section 2.3 with the
+// spatial DSTs factored out):
+//     z_j = D^{-1} F^* G_j F D^2 F G_j F^* D^{-1} y_j,
+// D = diag(alpha^{t/n}), F = (1/sqrt n)[theta^{tk}], theta = exp(2 pi i/n),
+// G_j = diag_k Sigma_{k,j}^{-1/2}, Sigma_{k,j} = Lambda_j lambda_{1,k} + lambda_{2,k}.
+// With FFT = sum_t exp(-2 pi i tk/n): F^* = FFT/sqrt(n) and F = sqrt(n) iFFT, so
+// for real y the map is: D^{-1}; FFT; x G; iFFT; D^2; FFT; x conj(G); iFFT; D^{-1}
+// (the second pass, F G F^*, equals iFFT(conj(G) FFT(.)) on real data).
+//
+// Two real modes a, b share one complex sequence z = y_a + i y_b.  With
+// Z = FFT(z), multiplying mode a by G_a and mode b by G_b is
+//     Y_k = A_k Z_k + B_k conj(Z_{n-k}),  A = (G_a + G_b)/(2n), B = (G_a - G_b)/(2n)
+// (1/n of the inverse FFT folded in), and iFFT(Y) = result_a + i result_b.
+// G_{n-k} = conj(G_k) gives A_{n-k} = conj(A_k), B_{n-k} = conj(B_k), so the
+// table holds k = 0..n/2 only.  A CTA owns 2*NS consecutive modes, all n time
+// levels of them staged in shared memory (coalesced rows of the time-major vector).
+#include "aao_internal.cuh"
+#include "fft_smem.cuh"
+
+namespace aao {
+
+struct TimeArgs {
+  int m, n, npairs;
+};
+
+// Y_k = A Z + B conj(W) (CONJ: with conj(A), conj(B))
+template <bool CONJ, typename C>
+__device__ __forceinline__ C mix(C A, C B, C Z, C W) {
+  if (CONJ) { A.y = -A.y; B.y = -B.y; }
+  C Y;
+  Y.x = fma(A.x, Z.x, fma(-A.y, Z.y, fma(B.x, W.x, B.y * W.y)));
+  Y.y = fma(A.x, Z.y, fma(A.y, Z.x, fma(B.y, W.x, -(B.x * W.y))));
+  return Y;
+}
+
+template <bool CONJ, int L, int NS, int NT, typename C>
+__device__ __forceinline__ void mix_pass(C* cbuf, const C* __restrict__ ab, int npairs, int p0) {
+  constexpr int H = L / 2;
+  for (int task = threadIdx.x; task < NS * (H + 1); task += NT) {
+    const int q = task % NS, k = task / NS;
+    C A, B;
+    if (p0 + q < npairs) {  // tiles may extend past the last mode pair (zero data there)
+      const long long row = ((long long)k * npairs + p0 + q) * 2;
+      A = ab[row];
+      B = ab[row + 1];
+    } else {
+      A.x = A.y = B.x = B.y = 0;
+    }
+    C* s = cbuf + q * L;
+    if (k == 0 || k == H) {
+      const C Z = s[k];
+      s[k] = mix<CONJ>(A, B, Z, Z);
+    } else {
+      const C Zk = s[k], Zm = s[L - k];
+      s[k] = mix<CONJ>(A, B, Zk, Zm);
+      s[L - k] = mix<!CONJ>(A, B, Zm, Zk);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R, int L, int NS, int NT>
+__global__ void __launch_bounds__(NT) k_time(const R* in, R* out, TimeArgs a, PrecTables<R> tb) {
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* cbuf = reinterpret_cast<C*>(smem_raw);
+  C* tw = cbuf + NS * L;
+  R* dinv = reinterpret_cast<R*>(tw + L);
+  R* d2 = dinv + L;
+
+  const int tid = threadIdx.x;
+  const int m = a.m;
+  const int s0 = blockIdx.x * (2 * NS);
+  const long long rb = (long long)blockIdx.y * L * m;
+  for (int i = tid; i < L; i += NT) {
+    tw[i] = tb.tw_time[i];
+    dinv[i] = tb.dinv[i];
+    d2[i] = tb.d2[i];
+  }
+  __syncthreads();
+
+  // load and scale by D^{-1}
+  for (int task = tid; task < NS * L; task += NT) {
+    const int q = task % NS, t = task / NS;
+    const int sa = s0 + 2 * q;
+    const R* p = in + rb + (long long)t * m + sa;
+    const R di = dinv[t];
+    C z;
+    z.x = (sa < m) ? p[0] * di : R(0);
+    z.y = (sa + 1 < m) ? p[1] * di : R(0);
+    cbuf[q * L + t] = z;
+  }
+  __syncthreads();
+
+  const int p0 = blockIdx.x * NS;
+  fft_block<L, NS, NT, false>(cbuf, tw);
+  mix_pass<false, L, NS, NT>(cbuf, tb.ab, a.npairs, p0);
+  fft_block<L, NS, NT, true>(cbuf, tw);
+  for (int task = tid; task < NS * L; task += NT) {
+    const int q = task % NS, t = task / NS;
+    C z = cbuf[q * L + t];
+    z.x *= d2[t];
+    z.y *= d2[t];
+    cbuf[q * L + t] = z;
+  }
+  __syncthreads();
+  fft_block<L, NS, NT, false>(cbuf, tw);
+  mix_pass<true, L, NS, NT>(cbuf, tb.ab, a.npairs, p0);
+  fft_block<L, NS, NT, true>(cbuf, tw);
+
+  // scale by D^{-1} and store
+  for (int task = tid; task < NS * L; task += NT) {
+    const int q = task % NS, t = task / NS;
+    const int sa = s0 + 2 * q;
+    R* p = out + rb + (long long)t * m + sa;
+    const C z = cbuf[q * L + t];
+    const R di = dinv[t];
+    if (sa < m) p[0] = z.x * di;
+    if (sa + 1 < m) p[1] = z.y * di;
+  }
+}
+
+template <typename R, int L>
+static cudaError_t time_launch_L(const Plan& P, const R* in, R* out, int nrhs, cudaStream_t s) {
+  using C = typename Cplx<R>::T;
+  constexpr int NT = 256;
+  constexpr int NS = 4096 / L;
+  const size_t smem = sizeof(C) * (NS * L + L) + 2 * sizeof(R) * L;
+  TimeArgs a;
+  a.m = P.m;
+  a.n = P.n;
+  a.npairs = P.npairs;
+  auto kern = k_time<R, L, NS, NT>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
+  kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_time(const Plan& P, const R* in, R* out, int nrhs, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  switch (P.n) {
+    case 64: return time_launch_L<R, 64>(P, in, out, nrhs, s);
+    case 128: return time_launch_L<R, 128>(P, in, out, nrhs, s);
+    case 256: return time_launch_L<R, 256>(P, in, out, nrhs, s);
+    case 512: return time_launch_L<R, 512>(P, in, out, nrhs, s);
+    case 1024: return time_launch_L<R, 1024>(P, in, out, nrhs, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_time<double>(const Plan&, const double*, double*, int, cudaStream_t,
+                                         uint64_t*);
+template cudaError_t launch_time<float>(const Plan&, const float*, float*, int, cudaStream_t,
+                                        uint64_t*);
+
+}  // namespace aao

@@ -99,7 +99,7 @@ def test_Sigma_is_spectrum_of_C_alpha(d, N, n, alpha):
     L = S.L_matrix(d, N, tau)
     C = S.C_alpha_matrix(L, n, alpha).toarray()
     ev = np.linalg.eigvals(C)
-    Sig = F.Sigma(n, alpha, F.L_eigenvalues(d, N, tau)).ravel()
+    Sig = F.Sigma(n, alpha, F.L_eigenvalues_minus_one(d, N, tau)).ravel()
     # match as multisets
     used = np.zeros(len(ev), bool)
     for s in Sig:
@@ -108,6 +108,35 @@ def test_Sigma_is_spectrum_of_C_alpha(d, N, n, alpha):
         assert dist[k] < 1e-9 * max(1.0, abs(s))
         used[k] = True
     assert not np.any((np.abs(Sig.imag) < 1e-14) & (Sig.real <= 0))
+
+
+@pytest.mark.parametrize("n,alpha,tau,N", [(1024, 0.1, 1 / 1024, 63), (256, 1e-6, 1 / 256, 255),
+                                            (64, 1e-3, 1 / 64, 63), (512, 1e-2, 1 / 512, 511),
+                                            (128, 1.0, 1 / 128, 127)])
+def test_sigma_cancellation_free_form(n, alpha, tau, N):
+    """Sigma = (1 - a theta)^2 + (Lambda - 1)(1 + a^2 theta^2) equals the literal
+    Lambda lambda_1 + lambda_2 evaluated in 50-digit arithmetic (mpmath) to 1e-14
+    relative (plus a few ulps of the terms' size, which matters only at alpha = 1),
+    at sample points including the lowest modes where the literal FP64 formula cancels."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    lm1 = F.L_eigenvalues_minus_one(1, N, tau)
+    Sig = F.Sigma(n, alpha, lm1)
+    h = mp.mpf(1) / (N + 1)
+    worst = 0.0
+    for k in [0, 1, 2, n // 4, n // 2 - 1, n // 2, n - 1]:
+        for j in [0, 1, N // 2, N - 1]:
+            mu = 4 / h ** 2 * mp.sin((j + 1) * mp.pi * h / 2) ** 2
+            lam = 1 + mp.mpf(tau) ** 2 / 2 * mu
+            a = mp.power(mp.mpf(alpha), mp.mpf(1) / n)
+            th = mp.exp(2j * mp.pi * k / n)
+            exact = lam * (1 + a * a * th * th) - 2 * a * th
+            # size of the two terms of the rewritten form: at alpha = 1 they can cancel
+            # for real (the ABC near-singularity), so allow a few ulps of that size
+            scale = abs((1 - a * th) ** 2) + abs((lam - 1) * (1 + a * a * th * th))
+            err = float(abs(Sig[k, j] - complex(exact)))
+            worst = max(worst, err / float(1e-14 * abs(exact) + 4e-16 * scale))
+    assert worst <= 1.0, worst
 
 
 def test_appendix_A_eigenvalue_form():
@@ -207,7 +236,7 @@ def test_alpha_one_is_abc_preconditioner():
     d, N, n = 1, 4, 6
     tau = 1.0 / n
     C = S.C_alpha_matrix(S.L_matrix(d, N, tau), n, 1.0).toarray()
-    Sig = F.Sigma(n, 1.0, F.L_eigenvalues(d, N, tau))
+    Sig = F.Sigma(n, 1.0, F.L_eigenvalues_minus_one(d, N, tau))
     assert np.abs(Sig).min() > 1e-3 and not np.any((np.abs(Sig.imag) < 1e-12) & (Sig.real <= 0))
     P1 = D.P_alpha_dense(C).real
     A = D.abs_sym(C)
