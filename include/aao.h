@@ -164,6 +164,17 @@ aao_status aao_apply_time(aao_handle* h, const double* x, double* y, int nrhs, v
 aao_status aao_minres_solve(aao_handle* h, const double* b, double* x, int use_x0, int nrhs,
                             double rtol, int maxit, aao_solve_info* info, void* stream);
 
+/* relres[r] = ||b_r - Y T x_r||_2 / ||b_r||_2 for every right-hand side r: the
+ * true relative residual that aao_minres_solve stops on (Section 3: MINRES with
+ * a relative-residual stopping rule; Y T as in aao_apply_op).  If ||b_r|| = 0
+ * the absolute residual norm is returned.
+ *   b, x   : nrhs x n x m device vectors (inputs, unchanged).
+ *   relres : device array of nrhs doubles (output), written stream-ordered.
+ * Uses the handle's reduction workspace, so calls on one handle must not
+ * overlap.  Errors: AAO_EINVAL (null pointer, nrhs outside [1, nrhs_max]), AAO_ECUDA. */
+aao_status aao_residual_norm(aao_handle* h, const double* b, const double* x, double* relres,
+                             int nrhs, void* stream);
+
 /* End-to-end solve from HOST buffers: copies f, psi0, psi1 (host, any memory;
  * pinned for speed) to the device, builds b (aao_build_rhs), runs
  * aao_minres_solve from a zero guess, and copies u (host, nrhs x n x m) back.

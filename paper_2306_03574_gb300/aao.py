@@ -18,6 +18,7 @@ __all__ = [
     "AAO_ETIMEOUT", "AAO_PREC_FP64", "AAO_PREC_FP32_IR", "lib", "lib_path", "header_functions",
     "aao_create", "aao_destroy", "aao_workspace_bytes", "aao_build_rhs", "aao_apply_op",
     "aao_apply_prec", "aao_apply_dst", "aao_apply_time", "aao_minres_solve", "aao_solve_host",
+    "aao_residual_norm",
     "aao_launch_count", "aao_status_str", "aao_last_error", "aao_profile_enable", "aao_profile_read",
     "Solver",
 ]
@@ -87,6 +88,7 @@ def lib() -> ctypes.CDLL:
             "aao_minres_solve": ([p, p, p, i, i, d, i, ctypes.POINTER(aao_solve_info), p], i),
             "aao_solve_host": ([p, p, p, p, p, i, d, i, ctypes.POINTER(aao_solve_info), p], i),
             "aao_launch_count": ([p], ctypes.c_uint64),
+            "aao_residual_norm": ([p, p, p, p, i, p], i),
             "aao_status_str": ([i], ctypes.c_char_p),
             "aao_profile_enable": ([p, i], i),
             "aao_profile_read": ([p, ctypes.POINTER(aao_kernel_stat), i], i),
@@ -233,6 +235,11 @@ def aao_minres_solve(h, b, x, nrhs: int = 1, rtol: float = 1e-8, maxit: int = 10
     return st, [i.as_dict() for i in infos]
 
 
+def aao_residual_norm(h, b, x, relres, nrhs: int = 1, stream=None) -> None:
+    _check(lib().aao_residual_norm(h, _dev_ptr(b), _dev_ptr(x), _dev_ptr(relres), nrhs, _stream(stream)),
+           "aao_residual_norm")
+
+
 def aao_solve_host(h, f, psi0, psi1, u, nrhs: int = 1, rtol: float = 1e-8, maxit: int = 100,
                    stream=None) -> Tuple[int, list]:
     infos = (aao_solve_info * nrhs)()
@@ -286,6 +293,9 @@ class Solver:
 
     def build_rhs(self, f, psi0, psi1, b, stream=None):
         aao_build_rhs(self.h, f, psi0, psi1, b, self._nrhs(f), stream)
+
+    def residual_norm(self, b, x, relres, stream=None):
+        aao_residual_norm(self.h, b, x, relres, self._nrhs(b), stream)
 
     def solve(self, b, x, rtol=1e-8, maxit=100, use_x0=False, stream=None):
         return aao_minres_solve(self.h, b, x, self._nrhs(b), rtol, maxit, use_x0, stream)

@@ -633,6 +633,20 @@ aao_status aao_minres_solve(aao_handle* h, const double* b, double* x, int use_x
   return minres_core(h, b, x, use_x0, nrhs, rtol, maxit, info, s);
 }
 
+aao_status aao_residual_norm(aao_handle* h, const double* b, const double* x, double* relres,
+                             int nrhs, void* stream) {
+  AAO_TRY(check_call(h, nrhs));
+  if (!b || !x || !relres) return fail(AAO_EINVAL, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* p1 = h->partial;
+  double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
+  int nb = 0;
+  AAO_KL(h, KC_YT_RES, s, launch_yt(h->P, x, nullptr, b, p1, 2, nrhs, s, &h->launches, &nb));
+  AAO_KL(h, KC_DOT, s, launch_dot(h->P, b, b, p2, nrhs, s, &h->launches));
+  AAO_KL(h, KC_SCAL, s, launch_relres(p1, nb, p2, dot_blocks_per_rhs(h->P), relres, nrhs, s, &h->launches));
+  return AAO_OK;
+}
+
 aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, const double* psi1,
                           double* u, int nrhs, double rtol, int maxit, aao_solve_info* info,
                           void* stream) {

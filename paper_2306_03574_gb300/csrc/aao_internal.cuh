@@ -123,6 +123,9 @@ cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* 
 cudaError_t launch_scalars(int step, MinresScalars* sc, const double* partial, int nb,
                            const double* partial2, int nb2, const double* partial3, int nb3,
                            int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl);
+// relres[r] = sqrt(sum of p1 partials / sum of p2 partials) per right-hand side
+cudaError_t launch_relres(const double* p1, int nb1, const double* p2, int nb2, double* relres,
+                          int nrhs, cudaStream_t s, uint64_t* nl);
 cudaError_t launch_cast(const double* in, float* out, size_t count, cudaStream_t s, uint64_t* nl);
 cudaError_t launch_uncast(const float* in, double* out, size_t count, cudaStream_t s, uint64_t* nl);
 cudaError_t launch_axpy(double a, const double* x, double* y, size_t count, cudaStream_t s,

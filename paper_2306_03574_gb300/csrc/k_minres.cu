@@ -194,6 +194,15 @@ __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict_
   }
 }
 
+// relres[r] = sqrt(sum r^2 / sum b^2) (absolute norm if b = 0)
+__global__ void k_relres(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2,
+                         double* __restrict__ relres) {
+  const int r = blockIdx.x;
+  const double s1 = sum_partials(p1 + (long long)r * nb1, nb1);
+  const double s2 = sum_partials(p2 + (long long)r * nb2, nb2);
+  if (threadIdx.x == 0) relres[r] = (s2 > 0.0) ? sqrt(s1 / s2) : sqrt(s1);
+}
+
 inline dim3 vgrid(const Plan& P, int nrhs) {
   const long long len = (long long)P.n * P.m;
   long long b = (len + VNT - 1) / VNT;
@@ -234,6 +243,13 @@ cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* 
   long long nb = (len + VNT - 1) / VNT;
   if (nb > 152 * 8) nb = 152 * 8;
   k_sub<<<(unsigned)nb, VNT, 0, s>>>(a, b, y, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_relres(const double* p1, int nb1, const double* p2, int nb2, double* relres,
+                          int nrhs, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  k_relres<<<nrhs, 32, 0, s>>>(p1, nb1, p2, nb2, relres);
   return cudaGetLastError();
 }
 

@@ -311,3 +311,25 @@ def test_alpha_one_abc_mode():
         assert relerr(zt.cpu().numpy(), ref) < 1e-10
     finally:
         aao.aao_destroy(h)
+
+
+@pytest.mark.parametrize("d,N,nt,nrhs", [(1, 63, 64, 1), (2, 63, 128, 3), (3, 63, 64, 2), (2, 255, 256, 1)])
+def test_residual_norm_parity(d, N, nt, nrhs):
+    """aao_residual_norm == ||b - Y T x|| / ||b|| from the oracle operator, per rhs;
+    b = 0 gives the absolute norm."""
+    m = N ** d
+    tau = 1.0 / nt
+    b = W.random_field((nrhs, nt, m), seed=800 + N)
+    x = W.random_field((nrhs, nt, m), seed=801 + N) * 1e-3
+    if nrhs > 1:
+        b[1] = 0.0
+    with aao.Solver(d, N, nt, tau, 1e-2, nrhs_max=nrhs) as s:
+        rr = torch.empty(nrhs, dtype=torch.float64, device=DEV)
+        s.residual_norm(cu(b), cu(x), rr)
+        torch.cuda.synchronize()
+        got = rr.cpu().numpy()
+    for r in range(nrhs):
+        res = np.linalg.norm(b[r] - OS.apply_YT(x[r], d, N, tau))
+        nb = np.linalg.norm(b[r])
+        ref = res / nb if nb > 0 else res
+        assert abs(got[r] - ref) <= 1e-13 * ref
