@@ -175,6 +175,31 @@ aao_status aao_minres_solve(aao_handle* h, const double* b, double* x, int use_x
 aao_status aao_residual_norm(aao_handle* h, const double* b, const double* x, double* relres,
                              int nrhs, void* stream);
 
+/* Allocation-free variant of aao_residual_norm.  The paper has no counterpart:
+ * it is a library facility for callers that cannot allocate device memory at the
+ * point where they need a residual check -- e.g. plugin code inside a host
+ * framework whose pool allocator owns all device memory and forbids outside
+ * allocations, or a latency-critical loop where the implicit synchronisation of
+ * cudaMalloc/cudaFree is not acceptable.  It takes no handle (creating one
+ * allocates) and calls no cudaMalloc, cudaFree or other allocating routine.
+ *   grid, nt, tau : as for aao_create (host pointer for grid); any N >= 1, nt >= 1.
+ *   b, x          : nrhs x n x m device vectors (inputs); relres: nrhs device doubles (output).
+ *   nrhs          : 1..64.  Larger values return AAO_EINVAL: the scratch is a static
+ *                   device array of 32768 doubles (256 KiB, 512 partial sums per
+ *                   right-hand side) that every GPU loading the library holds until exit.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * partial sums (each call rewrites every slot it reads, so nothing needs
+ * clearing); calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race on it and must be serialised by the caller.
+ * Errors: AAO_EINVAL, AAO_ECUDA; text in aao_noalloc_last_error(). */
+aao_status aao_residual_norm_noalloc(const aao_grid* grid, int nt, double tau, const double* b,
+                                     const double* x, double* relres, int nrhs, void* stream);
+
+/* Thread-local text of the last aao_residual_norm_noalloc failure ("" if none). */
+const char* aao_noalloc_last_error(void);
+
 /* End-to-end solve from HOST buffers: copies f, psi0, psi1 (host, any memory;
  * pinned for speed) to the device, builds b (aao_build_rhs), runs
  * aao_minres_solve from a zero guess, and copies u (host, nrhs x n x m) back.

@@ -18,7 +18,7 @@ __all__ = [
     "AAO_ETIMEOUT", "AAO_PREC_FP64", "AAO_PREC_FP32_IR", "lib", "lib_path", "header_functions",
     "aao_create", "aao_destroy", "aao_workspace_bytes", "aao_build_rhs", "aao_apply_op",
     "aao_apply_prec", "aao_apply_dst", "aao_apply_time", "aao_minres_solve", "aao_solve_host",
-    "aao_residual_norm",
+    "aao_residual_norm", "aao_residual_norm_noalloc",
     "aao_launch_count", "aao_status_str", "aao_last_error", "aao_profile_enable", "aao_profile_read",
     "Solver",
 ]
@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
             "aao_solve_host": ([p, p, p, p, p, i, d, i, ctypes.POINTER(aao_solve_info), p], i),
             "aao_launch_count": ([p], ctypes.c_uint64),
             "aao_residual_norm": ([p, p, p, p, i, p], i),
+            "aao_residual_norm_noalloc": ([ctypes.POINTER(aao_grid), i, d, p, p, p, i, p], i),
+            "aao_noalloc_last_error": ([], ctypes.c_char_p),
             "aao_status_str": ([i], ctypes.c_char_p),
             "aao_profile_enable": ([p, i], i),
             "aao_profile_read": ([p, ctypes.POINTER(aao_kernel_stat), i], i),
@@ -238,6 +240,19 @@ def aao_minres_solve(h, b, x, nrhs: int = 1, rtol: float = 1e-8, maxit: int = 10
 def aao_residual_norm(h, b, x, relres, nrhs: int = 1, stream=None) -> None:
     _check(lib().aao_residual_norm(h, _dev_ptr(b), _dev_ptr(x), _dev_ptr(relres), nrhs, _stream(stream)),
            "aao_residual_norm")
+
+
+def aao_residual_norm_noalloc(dim, N, nt, tau, b, x, relres, nrhs: int = 1, c2: float = 1.0,
+                              stream=None, raw_status: bool = False):
+    """Allocation-free residual norm (no handle); see include/aao.h."""
+    g = aao_grid(dim, N, c2)
+    st = lib().aao_residual_norm_noalloc(ctypes.byref(g), nt, tau, _dev_ptr(b), _dev_ptr(x),
+                                         _dev_ptr(relres), nrhs, _stream(stream))
+    if raw_status:
+        return st
+    if st != AAO_OK:
+        raise AaoError(st, "aao_residual_norm_noalloc", lib().aao_noalloc_last_error().decode())
+    return st
 
 
 def aao_solve_host(h, f, psi0, psi1, u, nrhs: int = 1, rtol: float = 1e-8, maxit: int = 100,
