@@ -33,7 +33,23 @@ if ROOT not in sys.path:
 
 METRIC = ("MINRES solves/s & unknown·iters/s at rel-res 1e-8; "
           "precond-apply HBM GB/s vs 8 TB/s")
-WORKLOAD = dict(d=2, N=255, nt=256, alpha=1e-6, rtol=1e-8, maxit=100, seed=2)
+# Named workloads.  The default is the FP64 2D one; the others are the mixed-precision
+# and batched rows (run explicitly with --workload).
+WORKLOADS = {
+    "2d255_fp64": dict(d=2, N=255, nt=256, alpha=1e-6, rtol=1e-8, maxit=100, seed=2, nrhs=1,
+                       precision="fp64"),
+    "2d511_fp64": dict(d=2, N=511, nt=512, alpha=1e-6, rtol=1e-8, maxit=100, seed=3, nrhs=1,
+                       precision="fp64"),
+    "2d511_mixed": dict(d=2, N=511, nt=512, alpha=1e-6, rtol=1e-8, maxit=200, seed=3, nrhs=1,
+                        precision="fp32"),
+    "2d255_mixed": dict(d=2, N=255, nt=256, alpha=1e-6, rtol=1e-8, maxit=200, seed=2, nrhs=1,
+                        precision="fp32"),
+    "3d127x8_mixed": dict(d=3, N=127, nt=128, alpha=1e-6, rtol=1e-8, maxit=200, seed=4, nrhs=8,
+                          precision="fp32"),
+    "3d127x8_fp64": dict(d=3, N=127, nt=128, alpha=1e-6, rtol=1e-8, maxit=100, seed=4, nrhs=8,
+                         precision="fp64"),
+}
+WORKLOAD = dict(WORKLOADS["2d255_fp64"])
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -245,11 +261,15 @@ def run_reference(args, world, rank):
     return 0
 
 
-def workload_config(unknowns):
-    return {"workload": "2d_wave_N255_nt256_fp64_minres_relres1e-8", "d": 2, "N": WORKLOAD["N"],
-            "nt": WORKLOAD["nt"], "unknowns": unknowns, "alpha": WORKLOAD["alpha"],
-            "rtol": WORKLOAD["rtol"], "rhs": 1, "seed": WORKLOAD["seed"],
-            "l2": "inputs larger than L2: every vector is 133 MB (L2 126 MB), ~1.2 GB touched per step",
+def workload_config(unknowns, name=None):
+    W_ = WORKLOAD
+    vec_mb = unknowns * 8 / 1e6
+    return {"workload": f"{W_['d']}d_wave_N{W_['N']}_nt{W_['nt']}_x{W_['nrhs']}_{W_['precision']}"
+                        f"_minres_relres{W_['rtol']:g}",
+            "name": name or "2d255_fp64", "d": W_["d"], "N": W_["N"], "nt": W_["nt"],
+            "unknowns": unknowns, "alpha": W_["alpha"], "rtol": W_["rtol"], "rhs": W_["nrhs"],
+            "precision": W_["precision"], "seed": W_["seed"],
+            "l2": f"inputs larger than L2: every vector is {vec_mb:.0f} MB per rhs (L2 126 MB)",
             "parallelism": "replicas (one independent problem per GPU)"}
 
 
@@ -267,15 +287,26 @@ def run_gpu(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    p = W.config_2d(N=WORKLOAD["N"], nt=WORKLOAD["nt"], alpha=WORKLOAD["alpha"],
-                    seed=WORKLOAD["seed"] + 1000 * rank)
-    unknowns = p.nt * p.m
-    f = torch.from_numpy(p.f).to(dev)
-    psi0 = torch.from_numpy(p.psi0).to(dev)
-    psi1 = torch.from_numpy(p.psi1).to(dev)
-    b = torch.empty((p.nt, p.m), dtype=torch.float64, device=dev)
+    d, N, nt, nrhs = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["nt"], WORKLOAD["nrhs"]
+    seed = WORKLOAD["seed"] + 1000 * rank
+    if d == 3:
+        p, fb = W.config_3d_batched(N=N, nt=nt, nrhs=nrhs, seed=seed, alpha=WORKLOAD["alpha"])
+        fnp = fb
+        p0np = np.zeros((nrhs, p.m))
+        p1np = np.zeros((nrhs, p.m))
+    else:
+        p = W.config_2d(N=N, nt=nt, alpha=WORKLOAD["alpha"], seed=seed)
+        fnp = np.broadcast_to(p.f, (nrhs,) + p.f.shape).copy()
+        p0np = np.broadcast_to(p.psi0, (nrhs, p.m)).copy()
+        p1np = np.broadcast_to(p.psi1, (nrhs, p.m)).copy()
+    unknowns = p.nt * p.m * nrhs
+    f = torch.from_numpy(fnp).to(dev)
+    psi0 = torch.from_numpy(p0np).to(dev)
+    psi1 = torch.from_numpy(p1np).to(dev)
+    b = torch.empty((nrhs, p.nt, p.m), dtype=torch.float64, device=dev)
     x = torch.empty_like(b)
-    s = aao.Solver(2, p.N, p.nt, p.tau, p.alpha)
+    prec = aao.AAO_PREC_FP64 if WORKLOAD["precision"] == "fp64" else aao.AAO_PREC_FP32_IR
+    s = aao.Solver(d, p.N, p.nt, p.tau, p.alpha, precision=prec, nrhs_max=nrhs)
     rtol, maxit = WORKLOAD["rtol"], WORKLOAD["maxit"]
 
     def step():
@@ -283,7 +314,7 @@ def run_gpu(args, world, rank, local):
         st, info = s.solve(b, x, rtol=rtol, maxit=maxit, stream=stream)
         if st != aao.AAO_OK:
             raise RuntimeError(f"solve failed: {aao.aao_status_str(st)} {info}")
-        return info[0]
+        return max(info, key=lambda i: i["iters"])
 
     for _ in range(args.warmup):
         info = step()
@@ -310,7 +341,7 @@ def run_gpu(args, world, rank, local):
     aao.aao_profile_enable(s.h, False)
     clk = clocks.stop()
     ms_max = reduce_max(ms, world, dev)
-    value = world * args.steps / (ms_max / 1e3)
+    value = world * args.steps * nrhs / (ms_max / 1e3)
     it = float(np.mean(iters))
     relres = info["relres_true"]
 
@@ -318,7 +349,7 @@ def run_gpu(args, world, rank, local):
     kern = {k: {"launches": v[0], "total_ms": round(v[1], 4), "avg_ms": v[1] / max(v[0], 1),
                 "share": v[1] / max(sum(t for _, t in prof.values()), 1e-12)} for k, v in prof.items()}
     dom = max(kern, key=lambda k: kern[k]["total_ms"])
-    flops = algorithmic_flops(dom, 2, p.N, p.nt, unknowns)
+    flops = algorithmic_flops(dom, d, p.N, p.nt, unknowns)
     achieved = flops / (kern[dom]["avg_ms"] / 1e3) / 1e12
     peak = FP64_PEAK_TFLOPS if dom.endswith("f64") or dom.startswith("yt") else FP32_PEAK_TFLOPS
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -326,12 +357,12 @@ def run_gpu(args, world, rank, local):
                 "flops_per_launch": flops,
                 "peak_note": "FP64 CUDA-core peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
     for k in kern:
-        fl = algorithmic_flops(k, 2, p.N, p.nt, unknowns)
+        fl = algorithmic_flops(k, d, p.N, p.nt, unknowns)
         if fl:
             kern[k]["achieved_tflops"] = fl / (kern[k]["avg_ms"] / 1e3) / 1e12
     # preconditioner application as a whole, against HBM (16 B per unknown in + out)
-    prec_cls = [k for k in kern if k.startswith("dst") or k.startswith("time")]
-    applies = kern.get("time_f64", {}).get("launches", 0)
+    prec_cls = [k for k in kern if k.startswith("dst") or k.startswith("time") or k == "cast"]
+    applies = kern.get("time_f64", kern.get("time_f32", {})).get("launches", 0)
     prec_ms = sum(kern[k]["total_ms"] for k in prec_cls) / max(applies, 1)
     hbm = measured_peaks().get("hbm_gbs", 6777.0)
     prec = {"ms_per_apply": prec_ms, "algorithmic_bytes": 16 * unknowns,
@@ -340,10 +371,10 @@ def run_gpu(args, world, rank, local):
     prec["frac_of_8tbs"] = prec["hbm_gbs"] / 8000.0 if prec["hbm_gbs"] else None
 
     # ---- end to end through the C ABI with host buffers ----
-    fh = torch.from_numpy(p.f.copy()).pin_memory()
-    p0h = torch.from_numpy(p.psi0.copy()).pin_memory()
-    p1h = torch.from_numpy(p.psi1.copy()).pin_memory()
-    uh = torch.empty((p.nt, p.m), dtype=torch.float64).pin_memory()
+    fh = torch.from_numpy(fnp).pin_memory()
+    p0h = torch.from_numpy(p0np).pin_memory()
+    p1h = torch.from_numpy(p1np).pin_memory()
+    uh = torch.empty((nrhs, p.nt, p.m), dtype=torch.float64).pin_memory()
     s.solve_host(fh, p0h, p1h, uh, rtol=rtol, maxit=maxit, stream=stream)  # staging warm-up
     e2e_steps = max(1, min(args.steps, 20))
     barrier(world)
@@ -356,14 +387,14 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize(dev)
     t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
     barrier(world)
-    e2e = {"value": world * e2e_steps / t_e2e, "unit": "solves/s",
-           "h2d_bytes_per_step": 8 * (p.nt * p.m + 2 * p.m), "d2h_bytes_per_step": 8 * p.nt * p.m,
+    e2e = {"value": world * e2e_steps * nrhs / t_e2e, "unit": "solves/s",
+           "h2d_bytes_per_step": 8 * nrhs * (p.nt * p.m + 2 * p.m), "d2h_bytes_per_step": 8 * nrhs * p.nt * p.m,
            "steps": e2e_steps, "api": "aao_solve_host"}
 
     out = None
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == "2d255_fp64":
             pp, pc, A = oracle_problem()
             t_full, it_o = oracle_full_solve(pp, pc, A)
             cpu = {"value": 1.0 / t_full, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -372,10 +403,13 @@ def run_gpu(args, world, rank, local):
         out = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(unknowns),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if WORKLOAD["precision"] == "fp64" else "f32+f64",
+            "data": "synthetic", "config": workload_config(unknowns, args.workload),
             "iters_per_solve": it, "relres_true": relres,
             "unknown_iters_per_s": world * unknowns * it * args.steps / (ms_max / 1e3),
+            "dtype_note": ("f64 throughout" if WORKLOAD["precision"] == "fp64" else
+                           "f32/complex64 preconditioner; f64 operator, MINRES recurrences and refinement"),
             "prec_apply": prec, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "kernels": kern,
         }
@@ -391,7 +425,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2d255_fp64")
+    ap.add_argument("--alpha", type=float, default=None)
     args = ap.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
+    if args.alpha is not None:
+        WORKLOAD["alpha"] = args.alpha
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     if args.impl == "reference":

@@ -65,6 +65,10 @@ struct aao_handle {
   double* vT = nullptr; double* vv = nullptr; double* vvp = nullptr; double* vz = nullptr;
   double* vzn = nullptr; double* vw = nullptr; double* vwp = nullptr;
   double* vr = nullptr; double* vdx = nullptr;  // refinement (FP32_IR)
+  double* vbh = nullptr;                         // right-hand side in the DST basis
+  double* lam64 = nullptr;                       // Lambda_s, eigenvalues of L (m entries)
+  double* relres_dev = nullptr;                  // nrhs_max per-rhs residual norms
+  double* relres_host = nullptr;                 // pinned copy
   float* f32 = nullptr;                          // FP32 preconditioner buffer
   double* partial = nullptr; int partial_stride = 0;  // 3 * nrhs_max * partial_stride
   MinresScalars* sc = nullptr;
@@ -95,6 +99,7 @@ struct aao_handle {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     if (sc_host) cudaFreeHost(sc_host);
+    if (relres_host) cudaFreeHost(relres_host);
   }
   template <typename T>
   aao_status alloc(T** p, size_t count) {
@@ -206,9 +211,40 @@ aao_status prec_apply(aao_handle* h, const double* in, double* out, int nrhs, cu
   return AAO_OK;
 }
 
-// Preconditioned MINRES from x0 = (use_x0 ? x : 0) on Y T x = b; fills info.
-aao_status minres_core(aao_handle* h, const double* b, double* x, int use_x0, int nrhs, double rtol,
-                       int maxit, aao_solve_info* info, cudaStream_t s) {
+// ---------------------------------------------------------------------------
+// MINRES in the DST basis.
+//
+// U = S (x) .. (x) S is orthogonal and symmetric, so with x^ = (I (x) U) x,
+// b^ = (I (x) U) b the system Y T x = b is Y T^ x^ = b^ with T^ = T after L -> Lambda
+// (diagonal), and P_alpha^{-1} becomes its time part alone.  MINRES on the
+// transformed system produces the transformed iterates (inner products and 2-norms
+// are unchanged by U), so each iteration needs only the time pipeline and the
+// pointwise-in-space operator; the DSTs run on b at the start and on x^ at the end.
+// ---------------------------------------------------------------------------
+
+// time part of P^{-1} in the handle's precision: in -> out (FP64 vectors)
+aao_status time_apply(aao_handle* h, const double* in, double* out, int nrhs, cudaStream_t s) {
+  if (h->precision == AAO_PREC_FP64)
+    AAO_KL(h, KC_TIME64, s, launch_time<double>(h->P, in, out, nrhs, s, &h->launches));
+  else
+    AAO_KL(h, KC_TIME32, s, launch_time_mixed(h->P, in, out, nrhs, s, &h->launches));
+  return AAO_OK;
+}
+
+// (I (x) U) in -> out (FP64; out may equal in)
+aao_status dst_apply(aao_handle* h, const double* in, double* out, int nrhs, cudaStream_t s) {
+  AAO_KL(h, KC_DST_X64, s, launch_dst_axis<double>(h->P, in, out, 0, nrhs, s, &h->launches));
+  for (int ax = 1; ax < h->P.d; ++ax)
+    AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(h->P, out, out, ax, nrhs, s, &h->launches));
+  return AAO_OK;
+}
+
+// Preconditioned MINRES on Y T^ x^ = bh (DST basis) from x^ = (use_x0 ? xh : 0).
+// true_res: stop on the true relative residual ||bh - Y T^ x^|| / ||bh|| recomputed every
+// iteration (the solver's contract); otherwise on the recurrence estimate (inner
+// refinement solves, whose outer loop recomputes the residual).
+aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_x0, int nrhs,
+                           double rtol, int maxit, aao_solve_info* info, cudaStream_t s, bool true_res) {
   const Plan& P = h->P;
   const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
   double* T = h->vT; double* v = h->vv; double* vp = h->vvp; double* z = h->vz;
@@ -219,20 +255,21 @@ aao_status minres_core(aao_handle* h, const double* b, double* x, int use_x0, in
   int nb_yt = 0;
   const int nb_dot = dot_blocks_per_rhs(P);
   uint64_t* nl = &h->launches;
+  const double* lam = h->lam64;
 
   if (use_x0) {
-    AAO_KL(h, KC_YT, s, launch_yt(P, x, T, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
-    AAO_KL(h, KC_SUB, s, launch_sub(P, b, T, v, nrhs, s, nl));
+    AAO_KL(h, KC_YT, s, launch_ythat(P, lam, xh, T, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
+    AAO_KL(h, KC_SUB, s, launch_sub(P, bh, T, v, nrhs, s, nl));
   } else {
-    AAO_CK(cudaMemsetAsync(x, 0, vb, s));
-    AAO_CK(cudaMemcpyAsync(v, b, vb, cudaMemcpyDeviceToDevice, s));
+    AAO_CK(cudaMemsetAsync(xh, 0, vb, s));
+    AAO_CK(cudaMemcpyAsync(v, bh, vb, cudaMemcpyDeviceToDevice, s));
   }
   AAO_CK(cudaMemsetAsync(vp, 0, vb, s));
   AAO_CK(cudaMemsetAsync(w, 0, vb, s));
   AAO_CK(cudaMemsetAsync(wp, 0, vb, s));
-  AAO_TRY(prec_apply(h, v, z, nrhs, s));
+  AAO_TRY(time_apply(h, v, z, nrhs, s));
   AAO_KL(h, KC_DOT, s, launch_dot(P, z, v, p1, nrhs, s, nl));
-  AAO_KL(h, KC_DOT, s, launch_dot(P, b, b, p2, nrhs, s, nl));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, bh, bh, p2, nrhs, s, nl));
   AAO_KL(h, KC_DOT, s, launch_dot(P, v, v, p3, nrhs, s, nl));
   AAO_KL(h, KC_SCAL, s, launch_scalars(0, h->sc, p1, nb_dot, p2, nb_dot, p3, nb_dot, nrhs, rtol, maxit, s, nl));
   const size_t scb = (size_t)nrhs * sizeof(MinresScalars);
@@ -244,15 +281,19 @@ aao_status minres_core(aao_handle* h, const double* b, double* x, int use_x0, in
     return true;
   };
   for (int it = 0; it < maxit && !all_done(); ++it) {
-    AAO_KL(h, KC_YT_DOT, s, launch_yt(P, z, T, z, p1, 1, nrhs, s, nl, &nb_yt));
+    AAO_KL(h, KC_YT_DOT, s, launch_ythat(P, lam, z, T, z, p1, 1, nrhs, s, nl, &nb_yt));
     AAO_KL(h, KC_SCAL, s, launch_scalars(1, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
     AAO_KL(h, KC_VUPD, s, launch_vupdate(P, T, v, vp, h->sc, nrhs, s, nl));  // vp <- v_{j+1}
-    AAO_TRY(prec_apply(h, vp, zn, nrhs, s));
+    AAO_TRY(time_apply(h, vp, zn, nrhs, s));
     AAO_KL(h, KC_DOT, s, launch_dot(P, zn, vp, p1, nrhs, s, nl));
     AAO_KL(h, KC_SCAL, s, launch_scalars(2, h->sc, p1, nb_dot, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
-    AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, z, wp, w, x, h->sc, nrhs, s, nl));  // wp <- w_{j+1}
-    AAO_KL(h, KC_YT_RES, s, launch_yt(P, x, nullptr, b, p1, 2, nrhs, s, nl, &nb_yt));
-    AAO_KL(h, KC_SCAL, s, launch_scalars(3, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
+    AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, z, wp, w, xh, h->sc, nrhs, s, nl));  // wp <- w_{j+1}
+    if (true_res) {
+      AAO_KL(h, KC_YT_RES, s, launch_ythat(P, lam, xh, nullptr, bh, p1, 2, nrhs, s, nl, &nb_yt));
+      AAO_KL(h, KC_SCAL, s, launch_scalars(3, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
+    } else {
+      AAO_KL(h, KC_SCAL, s, launch_scalars(4, h->sc, p1, 0, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
+    }
     std::swap(v, vp);
     std::swap(z, zn);
     std::swap(w, wp);
@@ -274,27 +315,63 @@ aao_status minres_core(aao_handle* h, const double* b, double* x, int use_x0, in
     }
     if (st != AAO_OK && worst == AAO_OK) worst = st;
   }
+  return worst;
+}
+
+// ||b - Y T x|| / ||b|| per rhs in the physical basis (stencil), copied into info.
+aao_status physical_check(aao_handle* h, const double* b, const double* x, int nrhs, double rtol,
+                          aao_solve_info* info, aao_status* worst, cudaStream_t s) {
+  double* p1 = h->partial;
+  double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
+  int nb = 0;
+  AAO_KL(h, KC_YT_RES, s, launch_yt(h->P, x, nullptr, b, p1, 2, nrhs, s, &h->launches, &nb));
+  AAO_KL(h, KC_DOT, s, launch_dot(h->P, b, b, p2, nrhs, s, &h->launches));
+  AAO_KL(h, KC_SCAL, s, launch_relres(p1, nb, p2, dot_blocks_per_rhs(h->P), h->relres_dev, nrhs, s,
+                                      &h->launches));
+  AAO_CK(cudaMemcpyAsync(h->relres_host, h->relres_dev, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AAO_CK(cudaStreamSynchronize(s));
+  for (int r = 0; r < nrhs; ++r) {
+    if (info) info[r].relres_true = h->relres_host[r];
+    if (h->relres_host[r] > rtol && *worst == AAO_OK) *worst = AAO_ENOTCONV;
+    if (info && h->relres_host[r] > rtol && info[r].status == AAO_OK) info[r].status = AAO_ENOTCONV;
+  }
+  return AAO_OK;
+}
+
+// FP64 solve: DST b, MINRES in the DST basis, DST x^ back, physical residual check.
+aao_status solve_fp64(aao_handle* h, const double* b, double* x, int use_x0, int nrhs, double rtol,
+                      int maxit, aao_solve_info* info, cudaStream_t s) {
+  std::vector<aao_solve_info> loc(nrhs);
+  aao_solve_info* inf = info ? info : loc.data();
+  AAO_TRY(dst_apply(h, b, h->vbh, nrhs, s));
+  if (use_x0) AAO_TRY(dst_apply(h, x, x, nrhs, s));
+  aao_status worst = minres_spectral(h, h->vbh, x, use_x0, nrhs, rtol, maxit, inf, s, true);
+  AAO_TRY(dst_apply(h, x, x, nrhs, s));
+  AAO_TRY(physical_check(h, b, x, nrhs, rtol, inf, &worst, s));
   if (worst != AAO_OK) g_err = std::string("MINRES: ") + aao_status_str(worst);
   return worst;
 }
 
-// Mixed precision: FP64 iterative refinement around MINRES with the FP32 preconditioner.
+// Mixed precision: FP64 iterative refinement in the DST basis around MINRES whose
+// preconditioner (the time pipeline) runs in FP32/complex64.
 aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int nrhs, double rtol,
                     int maxit, aao_solve_info* info, cudaStream_t s) {
   const Plan& P = h->P;
   const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
-  const size_t cnt = (size_t)nrhs * h->vlen();
   double* p1 = h->partial;
   double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
   uint64_t* nl = &h->launches;
-  if (!use_x0) AAO_CK(cudaMemsetAsync(x, 0, vb, s));
-  std::vector<aao_solve_info> inner(nrhs), acc(nrhs);
-  for (int r = 0; r < nrhs; ++r) { acc[r] = aao_solve_info{0, AAO_ENOTCONV, 1.0, 1.0, 0, 0}; }
-  // ||b||^2
+  double* bh = h->vbh;
+  std::vector<aao_solve_info> inner(nrhs), loc(nrhs);
+  aao_solve_info* acc = info ? info : loc.data();
+  for (int r = 0; r < nrhs; ++r) acc[r] = aao_solve_info{0, AAO_ENOTCONV, 1.0, 1.0, 0, 0};
+  AAO_TRY(dst_apply(h, b, bh, nrhs, s));
+  if (use_x0) AAO_TRY(dst_apply(h, x, x, nrhs, s));
+  else AAO_CK(cudaMemsetAsync(x, 0, vb, s));
   const int nb_dot = dot_blocks_per_rhs(P);
-  AAO_KL(h, KC_DOT, s, launch_dot(P, b, b, p2, nrhs, s, nl));
-  std::vector<double> hp((size_t)nrhs * nb_dot);
-  AAO_CK(cudaMemcpyAsync(hp.data(), p2, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, bh, bh, p2, nrhs, s, nl));
+  std::vector<double> hp((size_t)nrhs * std::max(nb_dot, yt_blocks_per_rhs(P)));
+  AAO_CK(cudaMemcpyAsync(hp.data(), p2, (size_t)nrhs * nb_dot * sizeof(double), cudaMemcpyDeviceToHost, s));
   AAO_CK(cudaStreamSynchronize(s));
   std::vector<double> bn(nrhs, 0.0);
   for (int r = 0; r < nrhs; ++r) {
@@ -302,16 +379,15 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
     for (int i = 0; i < nb_dot; ++i) t += hp[(size_t)r * nb_dot + i];
     bn[r] = std::sqrt(t > 0 ? t : 1.0);
   }
-  const int max_ir = 30;
+  const int max_ir = 40;
   int total_its = 0;
-  aao_status worst = AAO_ENOTCONV;
   for (int ir = 0; ir < max_ir; ++ir) {
-    // r = b - Y T x (FP64), its norm
+    // r^ = b^ - Y T^ x^ in FP64 and its norm
     int nb_yt = 0;
-    AAO_KL(h, KC_YT, s, launch_yt(P, x, h->vT, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
-    AAO_KL(h, KC_SUB, s, launch_sub(P, b, h->vT, h->vr, nrhs, s, nl));
+    AAO_KL(h, KC_YT, s, launch_ythat(P, h->lam64, x, h->vT, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
+    AAO_KL(h, KC_SUB, s, launch_sub(P, bh, h->vT, h->vr, nrhs, s, nl));
     AAO_KL(h, KC_DOT, s, launch_dot(P, h->vr, h->vr, p1, nrhs, s, nl));
-    AAO_CK(cudaMemcpyAsync(hp.data(), p1, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AAO_CK(cudaMemcpyAsync(hp.data(), p1, (size_t)nrhs * nb_dot * sizeof(double), cudaMemcpyDeviceToHost, s));
     AAO_CK(cudaStreamSynchronize(s));
     bool all = true;
     double worst_rel = 0.0;
@@ -321,16 +397,15 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
       const double rel = std::sqrt(t) / bn[r];
       acc[r].relres_true = rel;
       acc[r].ir_steps = ir;
-      if (rel <= rtol) acc[r].status = AAO_OK; else all = false;
-      worst_rel = std::max(worst_rel, rel);
+      if (rel <= rtol) acc[r].status = AAO_OK;
+      else all = false;
+      if (acc[r].status != AAO_OK) worst_rel = std::max(worst_rel, rel);
     }
-    if (all) { worst = AAO_OK; break; }
-    if (total_its >= maxit) break;
-    // inner solve: Y T dx = r to a relative tolerance that reaches rtol overall
-    double inner_tol = std::max(rtol / worst_rel, 1e-6);
+    if (all || total_its >= maxit) break;
+    // inner solve Y T^ dx^ = r^ to the relative accuracy that reaches rtol overall
+    double inner_tol = std::max(0.5 * rtol / worst_rel, 1e-7);
     inner_tol = std::min(inner_tol, 1e-2);
-    aao_status st = minres_core(h, h->vr, h->vdx, 0, nrhs, inner_tol, maxit - total_its, inner.data(), s);
-    (void)st;
+    minres_spectral(h, h->vr, h->vdx, 0, nrhs, inner_tol, maxit - total_its, inner.data(), s, false);
     int its = 0;
     for (int r = 0; r < nrhs; ++r) {
       its = std::max(its, inner[r].iters);
@@ -338,18 +413,19 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
       acc[r].relres_est = inner[r].relres_est;
     }
     total_its += std::max(its, 1);
-    // x += dx, but only for the right-hand sides not yet converged
     for (int r = 0; r < nrhs; ++r) {
       if (acc[r].status == AAO_OK) continue;
-      AAO_KL(h, KC_AXPY, s, launch_axpy(1.0, h->vdx + (size_t)r * h->vlen(), x + (size_t)r * h->vlen(), h->vlen(), s, nl));
+      AAO_KL(h, KC_AXPY, s, launch_axpy(1.0, h->vdx + (size_t)r * h->vlen(), x + (size_t)r * h->vlen(),
+                                        h->vlen(), s, nl));
     }
   }
-  for (int r = 0; r < nrhs; ++r) {
-    if (info) info[r] = acc[r];
+  AAO_TRY(dst_apply(h, x, x, nrhs, s));
+  aao_status worst = AAO_OK;
+  for (int r = 0; r < nrhs; ++r)
     if (acc[r].status != AAO_OK && worst == AAO_OK) worst = (aao_status)acc[r].status;
-  }
-  (void)cnt;
-  if (worst != AAO_OK) g_err = std::string("MINRES (FP32 preconditioner + FP64 refinement): ") + aao_status_str(worst);
+  AAO_TRY(physical_check(h, b, x, nrhs, rtol, acc, &worst, s));
+  if (worst != AAO_OK)
+    g_err = std::string("MINRES (FP32 preconditioner + FP64 refinement): ") + aao_status_str(worst);
   return worst;
 }
 
@@ -448,9 +524,22 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     d2[t] = (double)expl(2.0L * la * (long double)t / (long double)nt);
   }
   const long double hl = 1.0L / (long double)M;
+  std::vector<long double> mul(P.N);
   for (int i = 0; i < P.N; ++i) {
     const long double sv = sinl((long double)(i + 1) * pi * hl / 2.0L);
-    mu[i] = (double)(4.0L / (hl * hl) * sv * sv);
+    mul[i] = 4.0L / (hl * hl) * sv * sv;
+    mu[i] = (double)mul[i];
+  }
+  // Lambda_s = 1 + (c2 tau^2/2) sum_axes mu(i_axis), lexicographic s (x fastest)
+  std::vector<double> lam((size_t)P.m);
+  {
+    const long double ct = 0.5L * (long double)grid->c2 * (long double)tau * (long double)tau;
+    for (long long s_ = 0; s_ < P.m; ++s_) {
+      long long rest = s_;
+      long double sum = 0.0L;
+      for (int ax = 0; ax < P.d; ++ax) { sum += mul[rest % P.N]; rest /= P.N; }
+      lam[(size_t)s_] = (double)(1.0L + ct * sum);
+    }
   }
 
   // ---- device allocations ----
@@ -472,7 +561,8 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   const size_t vl = (size_t)h->nrhs_max * (size_t)nt * P.m;
   if ((st = h->alloc(&h->vT, vl)) || (st = h->alloc(&h->vv, vl)) || (st = h->alloc(&h->vvp, vl)) ||
       (st = h->alloc(&h->vz, vl)) || (st = h->alloc(&h->vzn, vl)) || (st = h->alloc(&h->vw, vl)) ||
-      (st = h->alloc(&h->vwp, vl)))
+      (st = h->alloc(&h->vwp, vl)) || (st = h->alloc(&h->vbh, vl)) ||
+      (st = h->alloc(&h->lam64, (size_t)P.m)) || (st = h->alloc(&h->relres_dev, (size_t)h->nrhs_max)))
     return bail(st);
   if (fp32) {
     if ((st = h->alloc(&h->vr, vl)) || (st = h->alloc(&h->vdx, vl)) || (st = h->alloc(&h->f32, vl)))
@@ -482,9 +572,9 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   if ((st = h->alloc(&h->partial, (size_t)3 * h->nrhs_max * h->partial_stride)) ||
       (st = h->alloc(&h->sc, (size_t)h->nrhs_max)))
     return bail(st);
-  if (cudaMallocHost(&h->sc_host, sizeof(MinresScalars) * h->nrhs_max) != cudaSuccess) {
+  if (cudaMallocHost(&h->sc_host, sizeof(MinresScalars) * h->nrhs_max) != cudaSuccess ||
+      cudaMallocHost(&h->relres_host, sizeof(double) * h->nrhs_max) != cudaSuccess) {
     cudaGetLastError();
-    h->sc_host = nullptr;
     return bail(fail(AAO_ENOMEM, "cudaMallocHost failed"));
   }
 
@@ -496,6 +586,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     AAO_TRY(upload(d2, h->d264));
     AAO_TRY(upload(mu, d_mu));
     AAO_TRY(upload(wq, d_wq));
+    AAO_TRY(upload(lam, h->lam64));
     if (fp32) {
       AAO_TRY(upload(to_f2(twS), h->tw_space32));
       AAO_TRY(upload(to_f(sinw), h->sinw32));
@@ -630,7 +721,7 @@ aao_status aao_minres_solve(aao_handle* h, const double* b, double* x, int use_x
   if (!(rtol >= 0.0) || maxit < 1) return fail(AAO_EINVAL, "rtol must be >= 0 and maxit >= 1");
   cudaStream_t s = (cudaStream_t)stream;
   if (h->precision == AAO_PREC_FP32_IR) return solve_ir(h, b, x, use_x0, nrhs, rtol, maxit, info, s);
-  return minres_core(h, b, x, use_x0, nrhs, rtol, maxit, info, s);
+  return solve_fp64(h, b, x, use_x0, nrhs, rtol, maxit, info, s);
 }
 
 aao_status aao_residual_norm(aao_handle* h, const double* b, const double* x, double* relres,

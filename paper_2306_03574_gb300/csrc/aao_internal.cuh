@@ -84,6 +84,12 @@ cudaError_t launch_time(const Plan& P, const R* in, R* out, int nrhs, cudaStream
 cudaError_t launch_yt(const Plan& P, const double* x, double* y, const double* w, double* partial,
                       int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
 int yt_blocks_per_rhs(const Plan& P);
+// The operator in the DST basis (L -> diag(lam)); same modes and partial layout as launch_yt.
+cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, double* y, const double* w,
+                         double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
+// Time pipeline computed in FP32/complex64 on FP64 vectors (conversion in the load and store).
+cudaError_t launch_time_mixed(const Plan& P, const double* in, double* out, int nrhs, cudaStream_t s,
+                              uint64_t* nl);
 
 cudaError_t launch_build_rhs(const Plan& P, const double* f, const double* psi0, const double* psi1,
                              double* b, int nrhs, cudaStream_t s, uint64_t* nl);
@@ -119,7 +125,7 @@ cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* 
                        cudaStream_t s, uint64_t* nl);
 // scalar steps: 0 = init (after z1, partial = <z1,v1>, partial2 = <b,b>, partial3 = <v1,v1>),
 // 1 = delta (partial = <Az, z>), 2 = gamma + Givens (partial = <z_{j+1}, v_{j+1}>),
-// 3 = true residual check (partial = sum r^2)
+// 3 = true residual check (partial = sum r^2), 4 = recurrence-estimate check (no partial)
 cudaError_t launch_scalars(int step, MinresScalars* sc, const double* partial, int nb,
                            const double* partial2, int nb2, const double* partial3, int nb3,
                            int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl);

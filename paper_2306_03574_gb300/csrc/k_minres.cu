@@ -182,6 +182,16 @@ __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict_
     S.s = sn;
     S.iters += 1;
     S.relres_est = fabs(S.eta) / S.gam1;
+  } else if (step == 4) {
+    // stop on the recurrence estimate (inner solves of the refinement loop, whose
+    // outer loop recomputes the true residual)
+    if (S.relres_est <= S.rtol) {
+      S.done = 1;
+      S.status = AAO_OK;
+    } else if (S.iters >= S.maxit || S.gam == 0.0) {
+      S.done = 1;
+      S.status = AAO_ENOTCONV;
+    }
   } else if (step == 3) {
     S.relres_true = sqrt(s1 / S.bnorm2);
     if (S.relres_true <= S.rtol) {

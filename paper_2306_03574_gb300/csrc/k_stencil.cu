@@ -92,6 +92,49 @@ __global__ void __launch_bounds__(YT_NT) k_yt(const double* __restrict__ x, doub
   }
 }
 
+// The same operator in the DST basis: with U = S (x)..(x) S orthogonal and symmetric,
+// (I (x) U) Y T (I (x) U) is Y T with L replaced by diag(Lambda), so
+// (Y T^ v)_{n-1-i} = Lambda_s (v_i + v_{i-2}) - 2 v_{i-1} pointwise in s.  Modes as k_yt.
+template <int MODE>
+__global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, double* __restrict__ y,
+                                                 const double* __restrict__ w,
+                                                 double* __restrict__ partial,
+                                                 const double* __restrict__ lam, YtArgs a) {
+  const int s = blockIdx.x * YT_NT + threadIdx.x;
+  const int n = a.n, m = a.m;
+  const int i0 = blockIdx.y * YT_CH;
+  const int i1 = min(n, i0 + YT_CH);
+  const long long rb = (long long)blockIdx.z * n * m;
+  double acc = 0.0;
+  if (s < m) {
+    const double ls = lam[s];
+    const double* xr = x + rb + s;
+    double x1 = 0.0, x2 = 0.0;  // v_{i-1}, v_{i-2}
+    for (int i = max(0, i0 - 2); i < i1; ++i) {
+      const double xi = xr[(long long)i * m];
+      if (i >= i0) {
+        const double o = fma(-2.0, x1, ls * (xi + x2));
+        const long long idx = rb + (long long)(n - 1 - i) * m + s;
+        if (MODE != 2) y[idx] = o;
+        if (MODE == 1) acc = fma(o, w[idx], acc);
+        if (MODE == 2) {
+          const double r = w[idx] - o;
+          acc = fma(r, r, acc);
+        }
+      }
+      x2 = x1;
+      x1 = xi;
+    }
+  }
+  if (MODE != 0) {
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) {
+      const long long nb = (long long)gridDim.x * gridDim.y;
+      partial[blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
 // b[n-1-k] = tau^2 f^k for k >= 2; tau^2 f^1 - L psi0; tau^2 f^0/2 + tau psi1 + psi0.
 template <int D>
 __global__ void __launch_bounds__(YT_NT) k_rhs(const double* __restrict__ f,
@@ -156,6 +199,18 @@ cudaError_t launch_yt(const Plan& P, const double* x, double* y, const double* w
     case 3: yt_dispatch<3>(mode, g, s, x, y, w, partial, a); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, double* y, const double* w,
+                        double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb) {
+  if (nl) ++*nl;
+  const YtArgs a = make_args(P);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
+  if (nb) *nb = (int)(g.x * g.y);
+  if (mode == 0) k_ythat<0><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
+  else if (mode == 1) k_ythat<1><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
+  else k_ythat<2><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
   return cudaGetLastError();
 }
 

@@ -59,8 +59,8 @@ __device__ __forceinline__ void mix_pass(C* cbuf, const C* __restrict__ ab, int 
   __syncthreads();
 }
 
-template <typename R, int L, int NS, int NT>
-__global__ void __launch_bounds__(NT) k_time(const R* in, R* out, TimeArgs a, PrecTables<R> tb) {
+template <typename R, typename TIO, int L, int NS, int NT>
+__global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cbuf = reinterpret_cast<C*>(smem_raw);
@@ -83,11 +83,11 @@ __global__ void __launch_bounds__(NT) k_time(const R* in, R* out, TimeArgs a, Pr
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
     const int sa = s0 + 2 * q;
-    const R* p = in + rb + (long long)t * m + sa;
+    const TIO* p = in + rb + (long long)t * m + sa;
     const R di = dinv[t];
     C z;
-    z.x = (sa < m) ? p[0] * di : R(0);
-    z.y = (sa + 1 < m) ? p[1] * di : R(0);
+    z.x = (sa < m) ? R(p[0]) * di : R(0);
+    z.y = (sa + 1 < m) ? R(p[1]) * di : R(0);
     cbuf[q * L + t] = z;
   }
   __syncthreads();
@@ -112,16 +112,16 @@ __global__ void __launch_bounds__(NT) k_time(const R* in, R* out, TimeArgs a, Pr
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
     const int sa = s0 + 2 * q;
-    R* p = out + rb + (long long)t * m + sa;
+    TIO* p = out + rb + (long long)t * m + sa;
     const C z = cbuf[q * L + t];
     const R di = dinv[t];
-    if (sa < m) p[0] = z.x * di;
-    if (sa + 1 < m) p[1] = z.y * di;
+    if (sa < m) p[0] = TIO(z.x * di);
+    if (sa + 1 < m) p[1] = TIO(z.y * di);
   }
 }
 
-template <typename R, int L>
-static cudaError_t time_launch_L(const Plan& P, const R* in, R* out, int nrhs, cudaStream_t s) {
+template <typename R, typename TIO, int L>
+static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
   constexpr int NT = 256;
   constexpr int NS = 4096 / L;
@@ -130,24 +130,35 @@ static cudaError_t time_launch_L(const Plan& P, const R* in, R* out, int nrhs, c
   a.m = P.m;
   a.n = P.n;
   a.npairs = P.npairs;
-  auto kern = k_time<R, L, NS, NT>;
+  auto kern = k_time<R, TIO, L, NS, NT>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
   kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
   return cudaGetLastError();
 }
 
+template <typename R, typename TIO>
+static cudaError_t time_dispatch(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
+  switch (P.n) {
+    case 64: return time_launch_L<R, TIO, 64>(P, in, out, nrhs, s);
+    case 128: return time_launch_L<R, TIO, 128>(P, in, out, nrhs, s);
+    case 256: return time_launch_L<R, TIO, 256>(P, in, out, nrhs, s);
+    case 512: return time_launch_L<R, TIO, 512>(P, in, out, nrhs, s);
+    case 1024: return time_launch_L<R, TIO, 1024>(P, in, out, nrhs, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename R>
 cudaError_t launch_time(const Plan& P, const R* in, R* out, int nrhs, cudaStream_t s, uint64_t* nl) {
   if (nl) ++*nl;
-  switch (P.n) {
-    case 64: return time_launch_L<R, 64>(P, in, out, nrhs, s);
-    case 128: return time_launch_L<R, 128>(P, in, out, nrhs, s);
-    case 256: return time_launch_L<R, 256>(P, in, out, nrhs, s);
-    case 512: return time_launch_L<R, 512>(P, in, out, nrhs, s);
-    case 1024: return time_launch_L<R, 1024>(P, in, out, nrhs, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return time_dispatch<R, R>(P, in, out, nrhs, s);
+}
+
+cudaError_t launch_time_mixed(const Plan& P, const double* in, double* out, int nrhs, cudaStream_t s,
+                              uint64_t* nl) {
+  if (nl) ++*nl;
+  return time_dispatch<float, double>(P, in, out, nrhs, s);
 }
 
 template cudaError_t launch_time<double>(const Plan&, const double*, double*, int, cudaStream_t,
