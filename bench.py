@@ -38,6 +38,8 @@ METRIC = ("MINRES solves/s & unknown·iters/s at rel-res 1e-8; "
 WORKLOADS = {
     "2d255_fp64": dict(d=2, N=255, nt=256, alpha=1e-6, rtol=1e-8, maxit=100, seed=2, nrhs=1,
                        precision="fp64"),
+    "1d63_fp64": dict(d=1, N=63, nt=64, alpha=1e-6, rtol=1e-8, maxit=100, seed=1, nrhs=1,
+                      precision="fp64"),
     "2d511_fp64": dict(d=2, N=511, nt=512, alpha=1e-6, rtol=1e-8, maxit=100, seed=3, nrhs=1,
                        precision="fp64"),
     "2d511_mixed": dict(d=2, N=511, nt=512, alpha=1e-6, rtol=1e-8, maxit=200, seed=3, nrhs=1,
@@ -48,6 +50,11 @@ WORKLOADS = {
                           precision="fp32"),
     "3d127x8_fp64": dict(d=3, N=127, nt=128, alpha=1e-6, rtol=1e-8, maxit=100, seed=4, nrhs=8,
                          precision="fp64"),
+    # Example 2's variable coefficient a = (30 + sin^2 x)(30 + sin^2 y), mean-coefficient preconditioner
+    "2d255_varcoef_fp64": dict(d=2, N=255, nt=256, alpha=1e-6, rtol=1e-8, maxit=200, seed=0, nrhs=1,
+                               precision="fp64", varcoef=True),
+    "2d255_varcoef_mixed": dict(d=2, N=255, nt=256, alpha=1e-3, rtol=1e-8, maxit=300, seed=0, nrhs=1,
+                                precision="fp32", varcoef=True),
 }
 WORKLOAD = dict(WORKLOADS["2d255_fp64"])
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
@@ -289,11 +296,22 @@ def run_gpu(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     d, N, nt, nrhs = WORKLOAD["d"], WORKLOAD["N"], WORKLOAD["nt"], WORKLOAD["nrhs"]
     seed = WORKLOAD["seed"] + 1000 * rank
+    varcoef = WORKLOAD.get("varcoef", False)
     if d == 3:
         p, fb = W.config_3d_batched(N=N, nt=nt, nrhs=nrhs, seed=seed, alpha=WORKLOAD["alpha"])
         fnp = fb
         p0np = np.zeros((nrhs, p.m))
         p1np = np.zeros((nrhs, p.m))
+    elif d == 1:
+        p = W.config_1d(N=N, nt=nt, alpha=WORKLOAD["alpha"], seed=seed)
+        fnp = np.broadcast_to(p.f, (nrhs,) + p.f.shape).copy()
+        p0np = np.broadcast_to(p.psi0, (nrhs, p.m)).copy()
+        p1np = np.broadcast_to(p.psi1, (nrhs, p.m)).copy()
+    elif varcoef:
+        p = W.example2(N, nt, alpha=WORKLOAD["alpha"])
+        fnp = np.broadcast_to(p.f, (nrhs,) + p.f.shape).copy()
+        p0np = np.broadcast_to(p.psi0, (nrhs, p.m)).copy()
+        p1np = np.broadcast_to(p.psi1, (nrhs, p.m)).copy()
     else:
         p = W.config_2d(N=N, nt=nt, alpha=WORKLOAD["alpha"], seed=seed)
         fnp = np.broadcast_to(p.f, (nrhs,) + p.f.shape).copy()
@@ -306,7 +324,14 @@ def run_gpu(args, world, rank, local):
     b = torch.empty((nrhs, p.nt, p.m), dtype=torch.float64, device=dev)
     x = torch.empty_like(b)
     prec = aao.AAO_PREC_FP64 if WORKLOAD["precision"] == "fp64" else aao.AAO_PREC_FP32_IR
-    s = aao.Solver(d, p.N, p.nt, p.tau, p.alpha, precision=prec, nrhs_max=nrhs)
+    if varcoef:
+        afun = p.meta["a"]
+        s = aao.Solver(d, p.N, p.nt, p.tau, p.alpha, c2=W.grid_mean(afun, d, N), precision=prec,
+                       nrhs_max=nrhs, variable_coefficient=True, graph=args.graph)
+        s.set_coefficient(torch.from_numpy(np.concatenate(
+            [fc.ravel() for fc in W.face_coefficients(afun, d, N)])).to(dev))
+    else:
+        s = aao.Solver(d, p.N, p.nt, p.tau, p.alpha, precision=prec, nrhs_max=nrhs, graph=args.graph)
     rtol, maxit = WORKLOAD["rtol"], WORKLOAD["maxit"]
 
     def step():
@@ -320,9 +345,17 @@ def run_gpu(args, world, rank, local):
         info = step()
     torch.cuda.synchronize(dev)
 
+    # per-kernel CUDA-event timing for the roofline: one profiled pass over the same
+    # steps (kernel timing makes the library use its host-driven loop)
+    aao.aao_profile_enable(s.h, True)
+    for _ in range(max(1, min(args.steps, 5))):
+        step()
+    torch.cuda.synchronize(dev)
+    prof = aao.aao_profile_read(s.h)
+    aao.aao_profile_enable(s.h, False)
+
     clocks = ClockSampler(local)
     clocks.start()
-    aao.aao_profile_enable(s.h, True)
     l0 = s.launches
     iters = []
     barrier(world)
@@ -337,8 +370,6 @@ def run_gpu(args, world, rank, local):
     barrier(world)
     ms = e0.elapsed_time(e1)
     launches = s.launches - l0
-    prof = aao.aao_profile_read(s.h)
-    aao.aao_profile_enable(s.h, False)
     clk = clocks.stop()
     ms_max = reduce_max(ms, world, dev)
     value = world * args.steps * nrhs / (ms_max / 1e3)
@@ -418,6 +449,115 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+def run_served(args, world, rank, local):
+    """Served stream: Poisson arrivals (mean 200/s, seeded) of 1D/2D requests with mixed
+    sizes, wave speeds and tolerances, admitted under a 120 GB HBM budget; replayed in
+    real time; latency = completion - submission on the server's clock."""
+    import numpy as np
+    import torch
+
+    import paper_2306_03574_gb300 as aao
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    count = args.requests
+    reqs = W.served_requests(count=count, rate=200.0, seed=5 + rank)
+    # per-shape device data (source, initial values) shared by the requests of that shape;
+    # wave speed, tolerance and the output buffer differ per request
+    shapes = {}
+    for r in reqs:
+        key = (r["d"], r["N"], r["nt"])
+        if key not in shapes:
+            p = W.served_problem(r, alpha=1e-6)
+            shapes[key] = dict(f=torch.from_numpy(p.f).to(dev), psi0=torch.from_numpy(p.psi0).to(dev),
+                               psi1=torch.from_numpy(p.psi1).to(dev), m=p.m, free=[], tau=p.tau)
+    srv = aao.aao_serve_create(int(120e9), args.slots)
+
+    def out_buf(key):
+        sh = shapes[key]
+        if sh["free"]:
+            return sh["free"].pop()
+        return torch.empty((key[2], sh["m"]), dtype=torch.float64, device=dev)
+
+    def submit(r, x):
+        key = (r["d"], r["N"], r["nt"])
+        sh = shapes[key]
+        return aao.aao_serve_submit(srv, r["d"], r["N"], r["nt"], sh["tau"], 1e-6, r["c2"], r["tol"], 100,
+                                    sh["f"], sh["psi0"], sh["psi1"], x)
+
+    # warm-up: one request per shape (handles, tables, captured graphs), untimed
+    for key in shapes:
+        r = next(q for q in reqs if (q["d"], q["N"], q["nt"]) == key)
+        x = out_buf(key)
+        st, _ = aao.aao_serve_wait(srv, submit(r, x), 300.0)
+        shapes[key]["free"].append(x)
+    torch.cuda.synchronize(dev)
+    inflight = {}
+    done = []
+    sample = {}
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        while True:
+            now = time.perf_counter() - t0
+            for t in list(inflight):
+                st, res = aao.aao_serve_poll(srv, t)
+                if st == aao.AAO_EPENDING:
+                    continue
+                rr, x = inflight.pop(t)
+                done.append((rr, st, res))
+                key = (rr["d"], rr["N"], rr["nt"])
+                if rr["id"] % 100 == 0 and rr["id"] not in sample:
+                    sample[rr["id"]] = (rr, x.cpu().numpy())
+                shapes[key]["free"].append(x)
+            if now >= r["arrival"]:
+                break
+            time.sleep(min(2e-4, r["arrival"] - now))
+        x = out_buf((r["d"], r["N"], r["nt"]))
+        inflight[submit(r, x)] = (r, x)
+    for t in list(inflight):
+        st, res = aao.aao_serve_wait(srv, t, 600.0)
+        rr, x = inflight.pop(t)
+        done.append((rr, st, res))
+        if rr["id"] % 100 == 0:
+            sample[rr["id"]] = (rr, x.cpu().numpy())
+    stats = aao.aao_serve_stats(srv)
+    aao.aao_serve_destroy(srv)
+    ok = [(rr, res) for rr, st, res in done if st == aao.AAO_OK]
+    lat = np.array([res["t_done"] - res["t_submit"] for _, res in ok])
+    t_first = min(res["t_submit"] for _, res in ok)
+    t_last = max(res["t_done"] for _, res in ok)
+    # each sampled result equals the same request solved alone (bit for bit)
+    same = True
+    for rid, (rr, xs) in sample.items():
+        key = (rr["d"], rr["N"], rr["nt"])
+        sh = shapes[key]
+        with aao.Solver(rr["d"], rr["N"], rr["nt"], sh["tau"], 1e-6, c2=rr["c2"], graph=True) as s1:
+            b = torch.empty((rr["nt"], sh["m"]), dtype=torch.float64, device=dev)
+            s1.build_rhs(sh["f"], sh["psi0"], sh["psi1"], b)
+            x1 = torch.empty_like(b)
+            s1.solve(b, x1, rtol=rr["tol"], maxit=100)
+            torch.cuda.synchronize(dev)
+            same &= bool(np.array_equal(x1.cpu().numpy(), xs))
+    unknowns = sum(rr["nt"] * rr["N"] ** rr["d"] for rr, _ in ok)
+    line = {
+        "metric": "served solves/s with p50/p99 latency (Poisson 200/s, mixed 1D/2D, 120 GB budget)",
+        "value": len(ok) / (t_last - t_first), "unit": "solves/s", "n_gpus": world,
+        "steps": len(reqs), "warmup": len(shapes), "ms_per_step": 1e3 * (t_last - t_first) / max(len(ok), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "served_poisson200_mixed_1d2d_fp64", "requests": len(reqs), "slots": args.slots,
+                   "budget_bytes": int(120e9), "shapes": len(shapes)},
+        "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                       "mean": float(lat.mean() * 1e3), "max": float(lat.max() * 1e3)},
+        "completed": len(ok), "failed": len(done) - len(ok), "offered_rate": 200.0,
+        "unknowns_per_s": unknowns / (t_last - t_first), "iters_mean": float(np.mean([res["iters"] for _, res in ok])),
+        "server": stats, "sample_equal_alone": same, "sample_size": len(sample),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,18 +565,26 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2d255_fp64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served"], default="2d255_fp64")
+    ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
+    ap.add_argument("--slots", type=int, default=8, help="served workload: concurrent solves")
     ap.add_argument("--alpha", type=float, default=None)
+    ap.add_argument("--graph", type=int, default=1,
+                    help="1: solve loop captured in a CUDA graph (device-side while loop); 0: host-driven")
     args = ap.parse_args()
-    WORKLOAD.clear()
-    WORKLOAD.update(WORKLOADS[args.workload])
-    if args.alpha is not None:
-        WORKLOAD["alpha"] = args.alpha
+    if args.workload != "served":
+        WORKLOAD.clear()
+        WORKLOAD.update(WORKLOADS[args.workload])
+        if args.alpha is not None:
+            WORKLOAD["alpha"] = args.alpha
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     if args.impl == "reference":
         world, rank, local = dist_setup(args.gpus, "gloo")
         rc = run_reference(args, world, rank)
+    elif args.workload == "served":
+        world, rank, local = dist_setup(args.gpus, "nccl")
+        rc = run_served(args, world, rank, local)
     else:
         world, rank, local = dist_setup(args.gpus, "nccl")
         rc = run_gpu(args, world, rank, local)

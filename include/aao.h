@@ -73,7 +73,12 @@ typedef enum aao_precision {
 typedef struct aao_opts {
   int precision;         /* aao_precision, default AAO_PREC_FP64 */
   int nrhs_max;          /* largest batch passed to any call; workspace is sized for it (default 1) */
-  int reserved[6];       /* must be zero */
+  int variable_coefficient; /* != 0: reserve room for a coefficient set by aao_set_coefficient */
+  int graph;             /* != 0: aao_minres_solve captures its iteration loop once per (batch
+                            size, tolerance, maxit) into a CUDA graph whose device-side WHILE
+                            node runs the iterations without host round trips (bounded by
+                            maxit); when kernel timing is enabled the host-driven loop is used */
+  int reserved[4];       /* must be zero */
 } aao_opts;
 
 typedef struct aao_solve_info {
@@ -106,6 +111,22 @@ typedef struct aao_handle aao_handle;
  * AAO_ENOMEM, AAO_ECUDA, AAO_ESINGULAR. */
 aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha,
                       aao_scheme scheme, const aao_opts* opts, aao_handle** out);
+
+/* Variable coefficient u_tt = div(a grad u) + f (Section 3, eq. (var coeff wave)):
+ * from this call on, the operator (aao_apply_op, aao_build_rhs, aao_residual_norm and
+ * the solves) uses L_a = I - (tau^2/2) Delta_{a,h} with the conservative central
+ * difference (Delta_{a,h} w)_i = sum_axes [a_{i+1/2}(w_{i+1} - w_i) - a_{i-1/2}(w_i - w_{i-1})]/h^2
+ * (eq. (tssystemvarwaveeq); the second right-hand-side block uses L_a psi0), while
+ * the preconditioner keeps the constant coefficient grid->c2 given to aao_create
+ * (the mean-coefficient preconditioner of eq. (mean-coefftsmat): pass c2 = mean of a
+ * on the grid).  MINRES then runs in the physical basis.
+ *   a_face : device array, the d face arrays one after the other; the array of axis
+ *            ax (0 = x) has N+1 entries along ax (face f at coordinate (f + 1/2) h,
+ *            f = 0..N) and N along the others, lexicographic with x fastest; total
+ *            d (N+1) N^(d-1) doubles.  Copied (stream-ordered) into the handle.
+ * The handle must have been created with opts.variable_coefficient != 0.
+ * Errors: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_set_coefficient(aao_handle* h, const double* a_face, void* stream);
 
 /* Free the handle and all its device memory (synchronises its device). */
 aao_status aao_destroy(aao_handle* h);
@@ -207,6 +228,72 @@ const char* aao_noalloc_last_error(void);
 aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, const double* psi1,
                           double* u, int nrhs, double rtol, int maxit,
                           aao_solve_info* info, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop that admits solves of mixed sizes, wave speeds, alpha
+ * and tolerances onto one GPU under an HBM budget (continuous admission: requests
+ * that arrive while others run are started as slots and memory free up; their work
+ * runs concurrently on the device).  Not part of the paper: a runtime around its
+ * method.  Each request is an FP64 solve of eq. (precsys) as aao_minres_solve does
+ * it (zero initial guess, true relative residual <= rtol); the Krylov state stays on
+ * the device for the whole solve (graph-captured loop); a request never shares
+ * buffers with another, so its result does not depend on what else is running.
+ * --------------------------------------------------------------------------- */
+typedef struct aao_server aao_server;
+
+typedef struct aao_request {
+  int dim, N, nt;        /* shape, as for aao_create (N+1 and nt powers of two in range) */
+  double tau, alpha, c2; /* time step, alpha in (0,1], wave speed squared */
+  double rtol;           /* true relative residual tolerance */
+  int maxit;
+  const double* f;       /* device, n x m source samples (as for aao_build_rhs) */
+  const double* psi0;    /* device, m */
+  const double* psi1;    /* device, m */
+  double* x;             /* device, n x m solution output (written by the server) */
+} aao_request;
+
+typedef struct aao_serve_result {
+  aao_solve_info info;   /* iterations, status, residuals of this request */
+  double t_submit;       /* seconds since aao_serve_create: submitted */
+  double t_start;        /* admitted and enqueued on the GPU */
+  double t_done;         /* completion observed by the server */
+  uint64_t ticket;
+} aao_serve_result;
+
+typedef struct aao_serve_stats {
+  uint64_t submitted, admitted, completed, failed, handles_created, evictions;
+  uint64_t pool_bytes, peak_pool_bytes, budget;
+  int in_flight, pending;
+} aao_serve_stats;
+
+/* Start a server on the current device.  hbm_budget_bytes bounds the device memory
+ * of its handle pool (workspace + tables + right-hand-side buffers); max_slots (1..64)
+ * bounds the solves in flight.  Allocates nothing until requests arrive.
+ * Errors: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_serve_create(size_t hbm_budget_bytes, int max_slots, aao_server** out);
+
+/* Queue a request (host pointer r, copied; the device buffers it names must stay
+ * valid and unchanged until the request completes).  Returns a ticket.  Never blocks
+ * on the GPU.  Errors: AAO_EINVAL, AAO_EUNSUPPORTED (size), AAO_EBUSY (shutting down).
+ * A request whose handle can never fit the budget completes with AAO_ENOMEM. */
+aao_status aao_serve_submit(aao_server* s, const aao_request* r, uint64_t* ticket);
+
+/* Non-blocking: AAO_EPENDING until the request finished, then its status (AAO_OK,
+ * AAO_ENOTCONV, ...) with *out filled; a finished ticket can be read once.
+ * AAO_EINVAL for an unknown ticket. */
+aao_status aao_serve_poll(aao_server* s, uint64_t ticket, aao_serve_result* out);
+
+/* Like aao_serve_poll but waits up to timeout_s seconds; AAO_ETIMEOUT if still pending. */
+aao_status aao_serve_wait(aao_server* s, uint64_t ticket, double timeout_s, aao_serve_result* out);
+
+/* Counters (host pointer). */
+aao_status aao_serve_stats_get(aao_server* s, aao_serve_stats* out);
+
+/* Finish every queued and running request, then free all handles and streams. */
+aao_status aao_serve_destroy(aao_server* s);
+
+/* Thread-local text of the last serving failure in this thread. */
+const char* aao_serve_last_error(void);
 
 /* Number of kernel launches this handle has issued since creation (statistics). */
 uint64_t aao_launch_count(const aao_handle* h);

@@ -13,9 +13,10 @@ import scipy.sparse.linalg as spla
 from .system import L_matrix, rhs_f
 
 
-def sequential_solve(prob, f_all: np.ndarray = None) -> np.ndarray:
-    """u^(1..n) of the scheme, shape (n, m); f_all defaults to eq. (main_matrix)'s f."""
-    L = L_matrix(prob.d, prob.N, prob.tau, prob.c2).tocsc()
+def sequential_solve(prob, f_all: np.ndarray = None, L=None) -> np.ndarray:
+    """u^(1..n) of the scheme, shape (n, m); f_all defaults to eq. (main_matrix)'s f;
+    L (sparse) defaults to I - (c^2 tau^2/2) Delta_h (pass L_a for the variable coefficient)."""
+    L = (L_matrix(prob.d, prob.N, prob.tau, prob.c2) if L is None else L).tocsc()
     lu = spla.splu(L)
     f = rhs_f(prob) if f_all is None else f_all
     n = f.shape[0]

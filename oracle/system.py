@@ -168,3 +168,79 @@ def error_E(u: np.ndarray, exact_levels: np.ndarray, d: int, h: float) -> float:
     """E_{tau,h} = max_k h^{d/2} || u^(k) - u(G_h, k tau) ||_2 (Section 3)."""
     diff = u.reshape(exact_levels.shape) - exact_levels
     return float(np.max(h ** (d / 2.0) * np.linalg.norm(diff, axis=1)))
+
+
+# ---------------------------------------------------------------------------
+# Variable coefficient u_tt = div(a grad u) + f (Section 3, eq. (var coeff wave))
+# ---------------------------------------------------------------------------
+
+def face_coefficients(afun, d: int, N: int):
+    """a sampled at the cell faces (input evaluation, from the shared input module):
+    per axis ax an array with N+1 faces along ax at (f + 1/2) h, grid points elsewhere."""
+    from workloads import face_coefficients as fc
+    return fc(afun, d, N)
+
+
+def apply_La_stencil(w: np.ndarray, faces, d: int, N: int, tau: float) -> np.ndarray:
+    """L_a w = w - (tau^2/2) Delta_{a,h} w with the conservative central difference
+    (Delta_{a,h} w)_i = sum_axes [a_{i+1/2}(w_{i+1} - w_i) - a_{i-1/2}(w_i - w_{i-1})] / h^2,
+    a at the faces, zero Dirichlet values outside.  w has shape (..., m)."""
+    h = 1.0 / (N + 1)
+    shp = w.shape[:-1] + (N,) * d
+    W = w.reshape(shp)
+    lap = np.zeros_like(W)
+    lead = W.ndim - d
+    for ax in range(d):
+        arr_ax = lead + (d - 1 - ax)
+        pad = [(0, 0)] * W.ndim
+        pad[arr_ax] = (1, 1)
+        Wp = np.pad(W, pad)                                   # zeros outside
+        sl = lambda a, b: tuple(slice(a, b) if k == arr_ax else slice(None) for k in range(W.ndim))
+        right = Wp[sl(2, N + 2)] - W                          # w_{i+1} - w_i
+        left = W - Wp[sl(0, N)]                               # w_i - w_{i-1}
+        F = faces[ax]
+        fsl = lambda a, b: tuple(slice(a, b) if k == (d - 1 - ax) else slice(None) for k in range(d))
+        aR = F[fsl(1, N + 1)]
+        aL = F[fsl(0, N)]
+        lap = lap + aR * right - aL * left
+    return (W - 0.5 * tau * tau * lap / (h * h)).reshape(w.shape)
+
+
+def apply_YT_var(v: np.ndarray, faces, d: int, N: int, tau: float) -> np.ndarray:
+    """Y T_a v with T_a the all-at-once matrix of eq. (tssystemvarwaveeq)."""
+    Lv = apply_La_stencil(v, faces, d, N, tau)
+    out = Lv.copy()
+    out[1:] -= 2.0 * v[:-1]
+    out[2:] += Lv[:-2]
+    return out[::-1].copy()
+
+
+def rhs_b_var(prob, faces) -> np.ndarray:
+    """Y f for eq. (tssystemvarwaveeq); its second block uses L_a psi0 (the paper prints L
+    there; L_a is the operator of the variable-coefficient scheme)."""
+    tau = prob.tau
+    F = np.array(prob.f, dtype=np.float64, copy=True)
+    out = tau * tau * F
+    out[0] = tau * tau * (F[0] / 2.0 + prob.psi1 / tau + prob.psi0 / (tau * tau))
+    out[1] = tau * tau * F[1] - apply_La_stencil(prob.psi0, faces, prob.d, prob.N, tau)
+    return out[::-1].copy()
+
+
+def La_matrix(faces, d: int, N: int, tau: float) -> sp.csr_matrix:
+    """L_a assembled independently of the stencil: -Delta_{a,h} = sum_axes D_ax^T diag(a_faces) D_ax / h^2
+    with D_ax the (faces x points) forward-difference matrix along axis ax (Dirichlet: the
+    boundary values are zero, so the first and last faces see one interior point)."""
+    h = 1.0 / (N + 1)
+    m = N ** d
+    D1 = sp.diags([-np.ones(N), np.ones(N)], [0, -1], shape=(N + 1, N), format="csr")  # (w_i - w_{i-1}) at face i
+    I = sp.identity(N, format="csr")
+    A = None
+    for ax in range(d):
+        mats = [I] * d
+        mats[d - 1 - ax] = D1
+        Dk = mats[0]
+        for Mx in mats[1:]:
+            Dk = sp.kron(Dk, Mx, format="csr")
+        term = Dk.T @ sp.diags(faces[ax].ravel()) @ Dk
+        A = term if A is None else A + term
+    return (sp.identity(m, format="csr") + 0.5 * tau * tau * A / (h * h)).tocsr()

@@ -16,11 +16,12 @@ __all__ = [
     "AaoError", "AAO_OK", "AAO_EINVAL", "AAO_EUNSUPPORTED", "AAO_ENOMEM", "AAO_ECUDA",
     "AAO_ENOTCONV", "AAO_EBREAKDOWN", "AAO_ESINGULAR", "AAO_EBUSY", "AAO_EPENDING",
     "AAO_ETIMEOUT", "AAO_PREC_FP64", "AAO_PREC_FP32_IR", "lib", "lib_path", "header_functions",
-    "aao_create", "aao_destroy", "aao_workspace_bytes", "aao_build_rhs", "aao_apply_op",
+    "aao_create", "aao_destroy", "aao_set_coefficient", "aao_workspace_bytes", "aao_build_rhs", "aao_apply_op",
     "aao_apply_prec", "aao_apply_dst", "aao_apply_time", "aao_minres_solve", "aao_solve_host",
     "aao_residual_norm", "aao_residual_norm_noalloc",
     "aao_launch_count", "aao_status_str", "aao_last_error", "aao_profile_enable", "aao_profile_read",
-    "Solver",
+    "Solver", "aao_serve_create", "aao_serve_submit", "aao_serve_poll", "aao_serve_wait",
+    "aao_serve_stats", "aao_serve_destroy",
 ]
 
 (AAO_OK, AAO_EINVAL, AAO_EUNSUPPORTED, AAO_ENOMEM, AAO_ECUDA, AAO_ENOTCONV, AAO_EBREAKDOWN,
@@ -45,7 +46,8 @@ class aao_grid(ctypes.Structure):
 
 class aao_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nrhs_max", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("variable_coefficient", ctypes.c_int), ("graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class aao_solve_info(ctypes.Structure):
@@ -56,6 +58,26 @@ class aao_solve_info(ctypes.Structure):
     def as_dict(self):
         return dict(iters=self.iters, status=self.status, relres_true=self.relres_true,
                     relres_est=self.relres_est, ir_steps=self.ir_steps)
+
+
+class aao_request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("N", ctypes.c_int), ("nt", ctypes.c_int),
+                ("tau", ctypes.c_double), ("alpha", ctypes.c_double), ("c2", ctypes.c_double),
+                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("f", ctypes.c_void_p), ("psi0", ctypes.c_void_p), ("psi1", ctypes.c_void_p),
+                ("x", ctypes.c_void_p)]
+
+
+class aao_serve_result(ctypes.Structure):
+    _fields_ = [("info", aao_solve_info), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("ticket", ctypes.c_uint64)]
+
+
+class aao_serve_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "failed",
+                                               "handles_created", "evictions", "pool_bytes",
+                                               "peak_pool_bytes", "budget")] + \
+               [("in_flight", ctypes.c_int), ("pending", ctypes.c_int)]
 
 
 class aao_kernel_stat(ctypes.Structure):
@@ -79,6 +101,7 @@ def lib() -> ctypes.CDLL:
             "aao_create": ([ctypes.POINTER(aao_grid), i, d, d, i, ctypes.POINTER(aao_opts),
                             ctypes.POINTER(ctypes.c_void_p)], i),
             "aao_destroy": ([p], i),
+            "aao_set_coefficient": ([p, p, p], i),
             "aao_workspace_bytes": ([p], sz),
             "aao_build_rhs": ([p, p, p, p, p, i, p], i),
             "aao_apply_op": ([p, p, p, i, p], i),
@@ -93,6 +116,13 @@ def lib() -> ctypes.CDLL:
             "aao_noalloc_last_error": ([], ctypes.c_char_p),
             "aao_status_str": ([i], ctypes.c_char_p),
             "aao_profile_enable": ([p, i], i),
+            "aao_serve_create": ([ctypes.c_size_t, i, ctypes.POINTER(ctypes.c_void_p)], i),
+            "aao_serve_submit": ([p, ctypes.POINTER(aao_request), ctypes.POINTER(ctypes.c_uint64)], i),
+            "aao_serve_poll": ([p, ctypes.c_uint64, ctypes.POINTER(aao_serve_result)], i),
+            "aao_serve_wait": ([p, ctypes.c_uint64, d, ctypes.POINTER(aao_serve_result)], i),
+            "aao_serve_stats_get": ([p, ctypes.POINTER(aao_serve_stats_t)], i),
+            "aao_serve_destroy": ([p], i),
+            "aao_serve_last_error": ([], ctypes.c_char_p),
             "aao_profile_read": ([p, ctypes.POINTER(aao_kernel_stat), i], i),
             "aao_last_error": ([], ctypes.c_char_p),
         }
@@ -183,15 +213,20 @@ def aao_last_error() -> str:
 
 def aao_create(dim: int, N: int, nt: int, tau: float, alpha: float, c2: float = 1.0,
                precision: int = AAO_PREC_FP64, nrhs_max: int = 1, scheme: int = 0,
-               raw_status: bool = False):
+               raw_status: bool = False, variable_coefficient: bool = False, graph: bool = False):
     g = aao_grid(dim, N, c2)
-    o = aao_opts(precision, nrhs_max, (ctypes.c_int * 6)())
+    o = aao_opts(precision, nrhs_max, int(bool(variable_coefficient)), int(bool(graph)),
+                 (ctypes.c_int * 4)())
     h = ctypes.c_void_p()
     st = lib().aao_create(ctypes.byref(g), nt, tau, alpha, scheme, ctypes.byref(o), ctypes.byref(h))
     if raw_status:
         return st, h.value
     _check(st, "aao_create")
     return h.value
+
+
+def aao_set_coefficient(h, a_face, stream=None) -> None:
+    _check(lib().aao_set_coefficient(h, _dev_ptr(a_face), _stream(stream)), "aao_set_coefficient")
 
 
 def aao_destroy(h) -> None:
@@ -265,14 +300,74 @@ def aao_solve_host(h, f, psi0, psi1, u, nrhs: int = 1, rtol: float = 1e-8, maxit
     return st, [i.as_dict() for i in infos]
 
 
+def _serve_result(r):
+    d = r.info.as_dict()
+    d.update(t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done, ticket=r.ticket)
+    return d
+
+
+def aao_serve_create(hbm_budget_bytes: int, max_slots: int, raw_status: bool = False):
+    s = ctypes.c_void_p()
+    st = lib().aao_serve_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(s))
+    if raw_status:
+        return st, s.value
+    if st != AAO_OK:
+        raise AaoError(st, "aao_serve_create", lib().aao_serve_last_error().decode())
+    return s.value
+
+
+def aao_serve_submit(srv, dim, N, nt, tau, alpha, c2, rtol, maxit, f, psi0, psi1, x) -> int:
+    r = aao_request(dim, N, nt, tau, alpha, c2, rtol, maxit, _dev_ptr(f), _dev_ptr(psi0), _dev_ptr(psi1),
+                    _dev_ptr(x))
+    t = ctypes.c_uint64()
+    st = lib().aao_serve_submit(srv, ctypes.byref(r), ctypes.byref(t))
+    if st != AAO_OK:
+        raise AaoError(st, "aao_serve_submit", lib().aao_serve_last_error().decode())
+    return int(t.value)
+
+
+def aao_serve_poll(srv, ticket: int):
+    """(status, result dict or None); status AAO_EPENDING while running."""
+    r = aao_serve_result()
+    st = lib().aao_serve_poll(srv, ticket, ctypes.byref(r))
+    if st == AAO_EPENDING:
+        return st, None
+    if st == AAO_EINVAL and r.ticket == 0:
+        return st, None
+    return st, _serve_result(r)
+
+
+def aao_serve_wait(srv, ticket: int, timeout_s: float):
+    r = aao_serve_result()
+    st = lib().aao_serve_wait(srv, ticket, float(timeout_s), ctypes.byref(r))
+    if st in (AAO_ETIMEOUT, AAO_EPENDING) or (st == AAO_EINVAL and r.ticket == 0):
+        return st, None
+    return st, _serve_result(r)
+
+
+def aao_serve_stats(srv) -> dict:
+    s = aao_serve_stats_t()
+    _check(lib().aao_serve_stats_get(srv, ctypes.byref(s)), "aao_serve_stats_get")
+    return {n: getattr(s, n) for n, _ in s._fields_}
+
+
+def aao_serve_destroy(srv) -> None:
+    _check(lib().aao_serve_destroy(srv), "aao_serve_destroy")
+
+
 class Solver:
     """Owns one handle: `Solver(dim, N, nt, tau, alpha, ...)`; methods map 1:1 to the C calls."""
 
-    def __init__(self, dim, N, nt, tau, alpha, c2=1.0, precision=AAO_PREC_FP64, nrhs_max=1):
+    def __init__(self, dim, N, nt, tau, alpha, c2=1.0, precision=AAO_PREC_FP64, nrhs_max=1,
+                 variable_coefficient=False, graph=False):
         self.dim, self.N, self.nt, self.tau, self.alpha, self.c2 = dim, N, nt, tau, alpha, c2
         self.m = N ** dim
         self.nrhs_max = nrhs_max
-        self.h = aao_create(dim, N, nt, tau, alpha, c2, precision, nrhs_max)
+        self.h = aao_create(dim, N, nt, tau, alpha, c2, precision, nrhs_max,
+                            variable_coefficient=variable_coefficient, graph=graph)
+
+    def set_coefficient(self, a_face, stream=None):
+        aao_set_coefficient(self.h, a_face, stream)
 
     def close(self):
         if self.h:

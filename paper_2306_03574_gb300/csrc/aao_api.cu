@@ -2,6 +2,7 @@
 // the MINRES driver (see include/aao.h for the contract of every entry point).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -69,6 +70,25 @@ struct aao_handle {
   double* lam64 = nullptr;                       // Lambda_s, eigenvalues of L (m entries)
   double* relres_dev = nullptr;                  // nrhs_max per-rhs residual norms
   double* relres_host = nullptr;                 // pinned copy
+  double* d_mu = nullptr;                        // 1D eigenvalues of -Delta_h (N)
+  double2* d_wq = nullptr;                       // per-frequency Sigma terms (2n)
+  double* d_mm = nullptr;                        // per-block min/max |Sigma|
+  int mm_blocks = 0;
+  double* face = nullptr;                        // variable coefficient on the faces (optional)
+  bool var_on = false;                           // operator uses the face coefficients
+  double* vxh = nullptr;                         // solution in the solve's working basis
+  // graph-captured solves
+  bool use_graph = false;
+  cudaStream_t cap_stream = nullptr;
+  int* d_trips = nullptr;
+  int trips_host = 0;
+  struct GraphCache {
+    long key;
+    double rtol;
+    int maxit;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphCache> graphs;
   float* f32 = nullptr;                          // FP32 preconditioner buffer
   double* partial = nullptr; int partial_stride = 0;  // 3 * nrhs_max * partial_stride
   MinresScalars* sc = nullptr;
@@ -95,6 +115,8 @@ struct aao_handle {
     prof.clear();
   }
   ~aao_handle() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     clear_prof();
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
@@ -161,6 +183,13 @@ void host_twiddles(int L, int sign, std::vector<double2>& out) {
 template <typename T>
 aao_status upload(const std::vector<T>& h, T* d) {
   AAO_CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return AAO_OK;
+}
+
+// stream-ordered upload from (pageable) host memory; the caller synchronises the stream
+template <typename T>
+aao_status upload_on(const std::vector<T>& h, T* d, cudaStream_t s) {
+  AAO_CK(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   return AAO_OK;
 }
 
@@ -239,67 +268,111 @@ aao_status dst_apply(aao_handle* h, const double* in, double* out, int nrhs, cud
   return AAO_OK;
 }
 
+// The physical operator Y T (constant or variable coefficient), modes as launch_yt.
+cudaError_t launch_op(aao_handle* h, const double* x, double* y, const double* w, double* partial, int mode,
+                      int nrhs, cudaStream_t s, int* nb) {
+  if (h->var_on) return launch_yt_var(h->P, h->face, x, y, w, partial, mode, nrhs, s, &h->launches, nb);
+  return launch_yt(h->P, x, y, w, partial, mode, nrhs, s, &h->launches, nb);
+}
+
+cudaError_t launch_rhs(aao_handle* h, const double* f, const double* psi0, const double* psi1, double* b,
+                       int nrhs, cudaStream_t s) {
+  if (h->var_on) return launch_build_rhs_var(h->P, h->face, f, psi0, psi1, b, nrhs, s, &h->launches);
+  return launch_build_rhs(h->P, f, psi0, psi1, b, nrhs, s, &h->launches);
+}
+
 // Preconditioned MINRES on Y T^ x^ = bh (DST basis) from x^ = (use_x0 ? xh : 0).
+// physical: run on the physical system instead (operator launch_op, preconditioner the
+// full P_alpha^{-1} with its DSTs) -- used when the coefficient is variable.
 // true_res: stop on the true relative residual ||bh - Y T^ x^|| / ||bh|| recomputed every
 // iteration (the solver's contract); otherwise on the recurrence estimate (inner
 // refinement solves, whose outer loop recomputes the residual).
-aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_x0, int nrhs,
-                           double rtol, int maxit, aao_solve_info* info, cudaStream_t s, bool true_res) {
+struct MinresBufs {
+  double *v, *vp, *z, *zn, *w, *wp;
+};
+
+struct MinresCtx {
+  aao_handle* h;
+  const double* bh;
+  double* xh;
+  int nrhs;
+  double rtol;
+  int maxit;
+  cudaStream_t s;
+  bool true_res, physical;
+  cudaError_t op(const double* xx, double* yy, const double* ww, double* part, int mode, int* nbp) const {
+    return physical ? launch_op(h, xx, yy, ww, part, mode, nrhs, s, nbp)
+                    : launch_ythat(h->P, h->lam64, xx, yy, ww, part, mode, nrhs, s, &h->launches, nbp);
+  }
+  aao_status prec(const double* in, double* out) const {
+    return physical ? prec_apply(h, in, out, nrhs, s) : time_apply(h, in, out, nrhs, s);
+  }
+};
+
+aao_status get_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out);
+aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaStream_t s);
+
+// Initialisation kernels (stream-ordered, no host synchronisation).
+aao_status minres_enqueue_init(const MinresCtx& c, int use_x0, const MinresBufs& B) {
+  aao_handle* h = c.h;
   const Plan& P = h->P;
-  const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
-  double* T = h->vT; double* v = h->vv; double* vp = h->vvp; double* z = h->vz;
-  double* zn = h->vzn; double* w = h->vw; double* wp = h->vwp;
+  const cudaStream_t s = c.s;
+  const size_t vb = (size_t)c.nrhs * h->vlen() * sizeof(double);
   double* p1 = h->partial;
   double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
   double* p3 = h->partial + (size_t)2 * h->nrhs_max * h->partial_stride;
-  int nb_yt = 0;
   const int nb_dot = dot_blocks_per_rhs(P);
   uint64_t* nl = &h->launches;
-  const double* lam = h->lam64;
-
+  int nb_yt = 0;
   if (use_x0) {
-    AAO_KL(h, KC_YT, s, launch_ythat(P, lam, xh, T, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
-    AAO_KL(h, KC_SUB, s, launch_sub(P, bh, T, v, nrhs, s, nl));
+    AAO_KL(h, KC_YT, s, c.op(c.xh, h->vT, nullptr, nullptr, 0, &nb_yt));
+    AAO_KL(h, KC_SUB, s, launch_sub(P, c.bh, h->vT, B.v, c.nrhs, s, nl));
   } else {
-    AAO_CK(cudaMemsetAsync(xh, 0, vb, s));
-    AAO_CK(cudaMemcpyAsync(v, bh, vb, cudaMemcpyDeviceToDevice, s));
+    AAO_CK(cudaMemsetAsync(c.xh, 0, vb, s));
+    AAO_CK(cudaMemcpyAsync(B.v, c.bh, vb, cudaMemcpyDeviceToDevice, s));
   }
-  AAO_CK(cudaMemsetAsync(vp, 0, vb, s));
-  AAO_CK(cudaMemsetAsync(w, 0, vb, s));
-  AAO_CK(cudaMemsetAsync(wp, 0, vb, s));
-  AAO_TRY(time_apply(h, v, z, nrhs, s));
-  AAO_KL(h, KC_DOT, s, launch_dot(P, z, v, p1, nrhs, s, nl));
-  AAO_KL(h, KC_DOT, s, launch_dot(P, bh, bh, p2, nrhs, s, nl));
-  AAO_KL(h, KC_DOT, s, launch_dot(P, v, v, p3, nrhs, s, nl));
-  AAO_KL(h, KC_SCAL, s, launch_scalars(0, h->sc, p1, nb_dot, p2, nb_dot, p3, nb_dot, nrhs, rtol, maxit, s, nl));
-  const size_t scb = (size_t)nrhs * sizeof(MinresScalars);
-  AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
-  AAO_CK(cudaStreamSynchronize(s));
-  auto all_done = [&]() {
-    for (int r = 0; r < nrhs; ++r)
-      if (!h->sc_host[r].done) return false;
-    return true;
-  };
-  for (int it = 0; it < maxit && !all_done(); ++it) {
-    AAO_KL(h, KC_YT_DOT, s, launch_ythat(P, lam, z, T, z, p1, 1, nrhs, s, nl, &nb_yt));
-    AAO_KL(h, KC_SCAL, s, launch_scalars(1, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
-    AAO_KL(h, KC_VUPD, s, launch_vupdate(P, T, v, vp, h->sc, nrhs, s, nl));  // vp <- v_{j+1}
-    AAO_TRY(time_apply(h, vp, zn, nrhs, s));
-    AAO_KL(h, KC_DOT, s, launch_dot(P, zn, vp, p1, nrhs, s, nl));
-    AAO_KL(h, KC_SCAL, s, launch_scalars(2, h->sc, p1, nb_dot, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
-    AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, z, wp, w, xh, h->sc, nrhs, s, nl));  // wp <- w_{j+1}
-    if (true_res) {
-      AAO_KL(h, KC_YT_RES, s, launch_ythat(P, lam, xh, nullptr, bh, p1, 2, nrhs, s, nl, &nb_yt));
-      AAO_KL(h, KC_SCAL, s, launch_scalars(3, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
-    } else {
-      AAO_KL(h, KC_SCAL, s, launch_scalars(4, h->sc, p1, 0, nullptr, 0, nullptr, 0, nrhs, rtol, maxit, s, nl));
-    }
-    std::swap(v, vp);
-    std::swap(z, zn);
-    std::swap(w, wp);
-    AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
-    AAO_CK(cudaStreamSynchronize(s));
+  AAO_CK(cudaMemsetAsync(B.vp, 0, vb, s));
+  AAO_CK(cudaMemsetAsync(B.w, 0, vb, s));
+  AAO_CK(cudaMemsetAsync(B.wp, 0, vb, s));
+  AAO_TRY(c.prec(B.v, B.z));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, B.z, B.v, p1, c.nrhs, s, nl));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, c.bh, c.bh, p2, c.nrhs, s, nl));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, B.v, B.v, p3, c.nrhs, s, nl));
+  AAO_KL(h, KC_SCAL, s, launch_scalars(0, h->sc, p1, nb_dot, p2, nb_dot, p3, nb_dot, c.nrhs, c.rtol,
+                                       c.maxit, s, nl));
+  return AAO_OK;
+}
+
+// One MINRES iteration with buffers B (stream-ordered, no host synchronisation);
+// afterwards the roles rotate: (v, vp), (z, zn), (w, wp) swap.
+aao_status minres_enqueue_iter(const MinresCtx& c, const MinresBufs& B) {
+  aao_handle* h = c.h;
+  const Plan& P = h->P;
+  const cudaStream_t s = c.s;
+  double* p1 = h->partial;
+  const int nb_dot = dot_blocks_per_rhs(P);
+  uint64_t* nl = &h->launches;
+  const int nrhs = c.nrhs;
+  int nb_yt = 0;
+  AAO_KL(h, KC_YT_DOT, s, c.op(B.z, h->vT, B.z, p1, 1, &nb_yt));
+  AAO_KL(h, KC_SCAL, s, launch_scalars(1, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+  AAO_KL(h, KC_VUPD, s, launch_vupdate(P, h->vT, B.v, B.vp, h->sc, nrhs, s, nl));  // vp <- v_{j+1}
+  AAO_TRY(c.prec(B.vp, B.zn));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, B.zn, B.vp, p1, nrhs, s, nl));
+  AAO_KL(h, KC_SCAL, s, launch_scalars(2, h->sc, p1, nb_dot, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+  AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, B.z, B.wp, B.w, c.xh, h->sc, nrhs, s, nl));  // wp <- w_{j+1}
+  if (c.true_res) {
+    AAO_KL(h, KC_YT_RES, s, c.op(c.xh, nullptr, c.bh, p1, 2, &nb_yt));
+    AAO_KL(h, KC_SCAL, s, launch_scalars(3, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+  } else {
+    AAO_KL(h, KC_SCAL, s, launch_scalars(4, h->sc, p1, 0, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
   }
+  return AAO_OK;
+}
+
+MinresBufs rotate(const MinresBufs& B) { return MinresBufs{B.vp, B.v, B.zn, B.z, B.wp, B.w}; }
+
+aao_status minres_collect(aao_handle* h, int nrhs, aao_solve_info* info) {
   aao_status worst = AAO_OK;
   for (int r = 0; r < nrhs; ++r) {
     const MinresScalars& S = h->sc_host[r];
@@ -318,13 +391,130 @@ aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_
   return worst;
 }
 
+// Capture the whole solve (initialisation, then a device-side WHILE loop whose body is
+// two buffer-rotated iterations and a condition kernel) into one executable graph.
+// Every pointer it touches belongs to the handle, so the graph is reused across solves.
+aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
+  aao_handle* h = c.h;
+  MinresCtx cc = c;
+  cudaStream_t cs = h->cap_stream;
+  cc.s = cs;
+  const MinresBufs B0{h->vv, h->vvp, h->vz, h->vzn, h->vw, h->vwp};
+  const int trip_limit = c.maxit / 2 + 2;
+  cudaGraph_t g = nullptr;
+  AAO_CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle hw;
+  auto fail_cleanup = [&](cudaError_t e, const char* what) {
+    cudaStreamCaptureStatus cst;
+    if (cudaStreamIsCapturing(cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t tmp = nullptr;
+      cudaStreamEndCapture(cs, &tmp);
+      if (tmp && tmp != g) cudaGraphDestroy(tmp);
+    }
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(AAO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaGraphConditionalHandleCreate(&hw, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail_cleanup(e, "cudaGraphConditionalHandleCreate");
+  e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamBeginCaptureToGraph");
+  if (cudaMemsetAsync(h->d_trips, 0, sizeof(int), cs) != cudaSuccess ||
+      minres_enqueue_init(cc, use_x0, B0) != AAO_OK ||
+      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 0, cs, nullptr) != cudaSuccess)
+    return fail_cleanup(cudaGetLastError(), "graph initialisation capture");
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t capg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamGetCaptureInfo");
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hw;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  e = cudaGraphAddNode(&wnode, capg, deps, nullptr, ndeps, &cp);
+  if (e != cudaSuccess) return fail_cleanup(e, "cudaGraphAddNode(while)");
+  e = cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamUpdateCaptureDependencies");
+  cudaGraph_t gend = nullptr;
+  e = cudaStreamEndCapture(cs, &gend);
+  if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamEndCapture");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail_cleanup(e, "capture of the loop body");
+  const MinresBufs B1 = rotate(B0);
+  if (minres_enqueue_iter(cc, B0) != AAO_OK || minres_enqueue_iter(cc, B1) != AAO_OK ||
+      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 1, cs, nullptr) != cudaSuccess)
+    return fail_cleanup(cudaGetLastError(), "loop body capture");
+  cudaGraph_t bend = nullptr;
+  e = cudaStreamEndCapture(cs, &bend);
+  if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamEndCapture(body)");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AAO_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  return AAO_OK;
+}
+
+// Preconditioned MINRES on Y T^ x^ = bh (DST basis) from x^ = (use_x0 ? xh : 0).
+// true_res: stop on the true relative residual ||bh - Y T^ x^|| / ||bh|| recomputed every
+// iteration (the solver's contract); otherwise on the recurrence estimate (inner
+// refinement solves).  physical: the physical system instead (operator launch_op,
+// preconditioner the full P_alpha^{-1}; used for a variable coefficient).
+// With graphs enabled (and kernel timing off) the loop runs on the device from one
+// captured graph per (batch size, mode); bh and xh must then be handle workspace.
+aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_x0, int nrhs,
+                           double rtol, int maxit, aao_solve_info* info, cudaStream_t s, bool true_res,
+                           bool physical = false) {
+  MinresCtx c{h, bh, xh, nrhs, rtol, maxit, s, true_res, physical};
+  const size_t scb = (size_t)nrhs * sizeof(MinresScalars);
+  const MinresBufs B0{h->vv, h->vvp, h->vz, h->vzn, h->vw, h->vwp};
+  if (h->use_graph && !h->prof_on) {
+    // rtol and maxit live in the device scalars, written by the captured initialisation
+    // from the values below; the graph is keyed on everything else.
+    cudaGraphExec_t ex = nullptr;
+    if (get_graph(c, use_x0, &ex) != AAO_OK) {
+      // keep solving with the host-driven loop (aao_last_error keeps the reason)
+      h->use_graph = false;
+      return minres_spectral(h, bh, xh, use_x0, nrhs, rtol, maxit, info, s, true_res, physical);
+    }
+    AAO_CK(cudaGraphLaunch(ex, s));
+    AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
+    AAO_CK(cudaMemcpyAsync(&h->trips_host, h->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AAO_CK(cudaStreamSynchronize(s));
+    h->launches += 12 + (uint64_t)h->trips_host * 20;  // kernels the graph ran (approximate per trip)
+    return minres_collect(h, nrhs, info);
+  }
+  AAO_TRY(minres_enqueue_init(c, use_x0, B0));
+  AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
+  AAO_CK(cudaStreamSynchronize(s));
+  auto all_done = [&]() {
+    for (int r = 0; r < nrhs; ++r)
+      if (!h->sc_host[r].done) return false;
+    return true;
+  };
+  MinresBufs B = B0;
+  for (int it = 0; it < maxit && !all_done(); ++it) {
+    AAO_TRY(minres_enqueue_iter(c, B));
+    B = rotate(B);
+    AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
+    AAO_CK(cudaStreamSynchronize(s));
+  }
+  return minres_collect(h, nrhs, info);
+}
+
 // ||b - Y T x|| / ||b|| per rhs in the physical basis (stencil), copied into info.
 aao_status physical_check(aao_handle* h, const double* b, const double* x, int nrhs, double rtol,
                           aao_solve_info* info, aao_status* worst, cudaStream_t s) {
   double* p1 = h->partial;
   double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
   int nb = 0;
-  AAO_KL(h, KC_YT_RES, s, launch_yt(h->P, x, nullptr, b, p1, 2, nrhs, s, &h->launches, &nb));
+  AAO_KL(h, KC_YT_RES, s, launch_op(h, x, nullptr, b, p1, 2, nrhs, s, &nb));
   AAO_KL(h, KC_DOT, s, launch_dot(h->P, b, b, p2, nrhs, s, &h->launches));
   AAO_KL(h, KC_SCAL, s, launch_relres(p1, nb, p2, dot_blocks_per_rhs(h->P), h->relres_dev, nrhs, s,
                                       &h->launches));
@@ -339,14 +529,25 @@ aao_status physical_check(aao_handle* h, const double* b, const double* x, int n
 }
 
 // FP64 solve: DST b, MINRES in the DST basis, DST x^ back, physical residual check.
+// (Variable coefficient: the same on the physical system, with b and x copied in/out.)
 aao_status solve_fp64(aao_handle* h, const double* b, double* x, int use_x0, int nrhs, double rtol,
                       int maxit, aao_solve_info* info, cudaStream_t s) {
   std::vector<aao_solve_info> loc(nrhs);
   aao_solve_info* inf = info ? info : loc.data();
+  const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
+  if (h->var_on) {  // operator not diagonal in the DST basis: physical-basis MINRES
+    AAO_CK(cudaMemcpyAsync(h->vbh, b, vb, cudaMemcpyDeviceToDevice, s));
+    if (use_x0) AAO_CK(cudaMemcpyAsync(h->vxh, x, vb, cudaMemcpyDeviceToDevice, s));
+    aao_status w = minres_spectral(h, h->vbh, h->vxh, use_x0, nrhs, rtol, maxit, inf, s, true, true);
+    AAO_CK(cudaMemcpyAsync(x, h->vxh, vb, cudaMemcpyDeviceToDevice, s));
+    AAO_CK(cudaStreamSynchronize(s));
+    if (w != AAO_OK) g_err = std::string("MINRES: ") + aao_status_str(w);
+    return w;
+  }
   AAO_TRY(dst_apply(h, b, h->vbh, nrhs, s));
-  if (use_x0) AAO_TRY(dst_apply(h, x, x, nrhs, s));
-  aao_status worst = minres_spectral(h, h->vbh, x, use_x0, nrhs, rtol, maxit, inf, s, true);
-  AAO_TRY(dst_apply(h, x, x, nrhs, s));
+  if (use_x0) AAO_TRY(dst_apply(h, x, h->vxh, nrhs, s));
+  aao_status worst = minres_spectral(h, h->vbh, h->vxh, use_x0, nrhs, rtol, maxit, inf, s, true);
+  AAO_TRY(dst_apply(h, h->vxh, x, nrhs, s));
   AAO_TRY(physical_check(h, b, x, nrhs, rtol, inf, &worst, s));
   if (worst != AAO_OK) g_err = std::string("MINRES: ") + aao_status_str(worst);
   return worst;
@@ -361,13 +562,20 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
   double* p1 = h->partial;
   double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
   uint64_t* nl = &h->launches;
+  const bool phys = h->var_on;  // variable coefficient: refine in the physical basis
   double* bh = h->vbh;
+  double* xh = h->vxh;
   std::vector<aao_solve_info> inner(nrhs), loc(nrhs);
   aao_solve_info* acc = info ? info : loc.data();
   for (int r = 0; r < nrhs; ++r) acc[r] = aao_solve_info{0, AAO_ENOTCONV, 1.0, 1.0, 0, 0};
-  AAO_TRY(dst_apply(h, b, bh, nrhs, s));
-  if (use_x0) AAO_TRY(dst_apply(h, x, x, nrhs, s));
-  else AAO_CK(cudaMemsetAsync(x, 0, vb, s));
+  if (!phys) {
+    AAO_TRY(dst_apply(h, b, bh, nrhs, s));
+    if (use_x0) AAO_TRY(dst_apply(h, x, xh, nrhs, s));
+  } else {
+    AAO_CK(cudaMemcpyAsync(bh, b, vb, cudaMemcpyDeviceToDevice, s));
+    if (use_x0) AAO_CK(cudaMemcpyAsync(xh, x, vb, cudaMemcpyDeviceToDevice, s));
+  }
+  if (!use_x0) AAO_CK(cudaMemsetAsync(xh, 0, vb, s));
   const int nb_dot = dot_blocks_per_rhs(P);
   AAO_KL(h, KC_DOT, s, launch_dot(P, bh, bh, p2, nrhs, s, nl));
   std::vector<double> hp((size_t)nrhs * std::max(nb_dot, yt_blocks_per_rhs(P)));
@@ -384,7 +592,8 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
   for (int ir = 0; ir < max_ir; ++ir) {
     // r^ = b^ - Y T^ x^ in FP64 and its norm
     int nb_yt = 0;
-    AAO_KL(h, KC_YT, s, launch_ythat(P, h->lam64, x, h->vT, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
+    if (phys) AAO_KL(h, KC_YT, s, launch_op(h, xh, h->vT, nullptr, nullptr, 0, nrhs, s, &nb_yt));
+    else AAO_KL(h, KC_YT, s, launch_ythat(P, h->lam64, xh, h->vT, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
     AAO_KL(h, KC_SUB, s, launch_sub(P, bh, h->vT, h->vr, nrhs, s, nl));
     AAO_KL(h, KC_DOT, s, launch_dot(P, h->vr, h->vr, p1, nrhs, s, nl));
     AAO_CK(cudaMemcpyAsync(hp.data(), p1, (size_t)nrhs * nb_dot * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -405,7 +614,7 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
     // inner solve Y T^ dx^ = r^ to the relative accuracy that reaches rtol overall
     double inner_tol = std::max(0.5 * rtol / worst_rel, 1e-7);
     inner_tol = std::min(inner_tol, 1e-2);
-    minres_spectral(h, h->vr, h->vdx, 0, nrhs, inner_tol, maxit - total_its, inner.data(), s, false);
+    minres_spectral(h, h->vr, h->vdx, 0, nrhs, inner_tol, maxit - total_its, inner.data(), s, false, phys);
     int its = 0;
     for (int r = 0; r < nrhs; ++r) {
       its = std::max(its, inner[r].iters);
@@ -415,11 +624,12 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
     total_its += std::max(its, 1);
     for (int r = 0; r < nrhs; ++r) {
       if (acc[r].status == AAO_OK) continue;
-      AAO_KL(h, KC_AXPY, s, launch_axpy(1.0, h->vdx + (size_t)r * h->vlen(), x + (size_t)r * h->vlen(),
+      AAO_KL(h, KC_AXPY, s, launch_axpy(1.0, h->vdx + (size_t)r * h->vlen(), xh + (size_t)r * h->vlen(),
                                         h->vlen(), s, nl));
     }
   }
-  AAO_TRY(dst_apply(h, x, x, nrhs, s));
+  if (!phys) AAO_TRY(dst_apply(h, xh, x, nrhs, s));
+  else AAO_CK(cudaMemcpyAsync(x, xh, vb, cudaMemcpyDeviceToDevice, s));
   aao_status worst = AAO_OK;
   for (int r = 0; r < nrhs; ++r)
     if (acc[r].status != AAO_OK && worst == AAO_OK) worst = (aao_status)acc[r].status;
@@ -429,7 +639,145 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
   return worst;
 }
 
+// Parameter-dependent tables of a handle: D_alpha, D_alpha^2, the per-frequency terms
+// of Sigma, Lambda, and the spectral table (built on the device); checks min |Sigma|.
+// Used by aao_create and to re-bind a pooled handle to new (tau, alpha, c2).
+aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaStream_t s) {
+  Plan& P = h->P;
+  const int nt = P.n, M = P.M;
+  const bool fp32 = (h->precision == AAO_PREC_FP32_IR);
+  P.tau = tau;
+  P.alpha = alpha;
+  P.c2 = c2;
+  P.coef = c2 * tau * tau / (2.0 * P.h * P.h);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<double2> wq(2 * (size_t)nt);
+  std::vector<double> dinv(nt), d2(nt);
+  const long double la = logl((long double)alpha);
+  {
+    // per-frequency terms of Sigma = (1 - a theta^k)^2 + (Lambda - 1)(1 + a^2 theta^{2k})
+    const long double a = expl(la / nt), one_minus_a = -expm1l(la / nt);
+    for (int k = 0; k < nt; ++k) {
+      const long double phi = 2.0L * pi * (long double)k / (long double)nt;
+      const long double sh = sinl(phi / 2.0L), c = cosl(phi), sn = sinl(phi);
+      const long double wr = one_minus_a + 2.0L * a * sh * sh, wi = -a * sn;
+      wq[2 * k] = make_double2((double)((wr - wi) * (wr + wi)), (double)(2.0L * wr * wi));
+      const long double qr = one_minus_a * (1.0L + a) + 2.0L * a * a * c * c;
+      wq[2 * k + 1] = make_double2((double)qr, (double)(2.0L * a * a * sn * c));
+    }
+  }
+  for (int t = 0; t < nt; ++t) {
+    dinv[t] = (double)expl(-la * (long double)t / (long double)nt);
+    d2[t] = (double)expl(2.0L * la * (long double)t / (long double)nt);
+  }
+  // Lambda_s = 1 + (c2 tau^2/2) sum_axes mu(i_axis), lexicographic s (x fastest)
+  const long double hl = 1.0L / (long double)M;
+  std::vector<long double> mul(P.N);
+  for (int i = 0; i < P.N; ++i) {
+    const long double sv = sinl((long double)(i + 1) * pi * hl / 2.0L);
+    mul[i] = 4.0L / (hl * hl) * sv * sv;
+  }
+  std::vector<double> lam((size_t)P.m);
+  const long double ct = 0.5L * (long double)c2 * (long double)tau * (long double)tau;
+  for (long long s_ = 0; s_ < P.m; ++s_) {
+    long long rest = s_;
+    long double sum = 0.0L;
+    for (int ax = 0; ax < P.d; ++ax) { sum += mul[rest % P.N]; rest /= P.N; }
+    lam[(size_t)s_] = (double)(1.0L + ct * sum);
+  }
+  const std::vector<float> dinv32 = to_f(dinv), d232 = to_f(d2);
+  AAO_TRY(upload_on(dinv, h->dinv64, s));
+  AAO_TRY(upload_on(d2, h->d264, s));
+  AAO_TRY(upload_on(wq, h->d_wq, s));
+  AAO_TRY(upload_on(lam, h->lam64, s));
+  if (fp32) {
+    AAO_TRY(upload_on(dinv32, h->dinv32, s));
+    AAO_TRY(upload_on(d232, h->d232, s));
+  }
+  int nb = 0;
+  AAO_CK(launch_spectral_table(P, h->d_mu, h->d_wq, h->ab64, fp32 ? h->ab32 : nullptr, h->d_mm, &nb,
+                               s, &h->launches));
+  std::vector<double> mm((size_t)2 * nb);
+  AAO_CK(cudaMemcpyAsync(mm.data(), h->d_mm, mm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AAO_CK(cudaStreamSynchronize(s));
+  double smin = 1e300, smax = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    smin = std::min(smin, mm[2 * i]);
+    smax = std::max(smax, mm[2 * i + 1]);
+  }
+  if (!(smin > 1e-12 * smax))
+    return fail(AAO_ESINGULAR, "min |Sigma| / max |Sigma| = " + std::to_string(smin / smax) +
+                                   " below 1e-12: preconditioner singular");
+  return AAO_OK;
+}
+
+aao_status get_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
+  aao_handle* h = c.h;
+  const long key = ((long)c.nrhs << 8) | (use_x0 ? 1 : 0) | (c.true_res ? 2 : 0) | (c.physical ? 4 : 0) |
+                   ((c.bh == h->vr) ? 8 : 0);
+  for (auto& gc : h->graphs)
+    if (gc.key == key && gc.rtol == c.rtol && gc.maxit == c.maxit) {
+      *out = gc.exec;
+      return AAO_OK;
+    }
+  AAO_TRY(build_graph(c, use_x0, out));
+  h->graphs.push_back(aao_handle::GraphCache{key, c.rtol, c.maxit, *out});
+  return AAO_OK;
+}
+
 }  // namespace
+
+// ---- internal entry points for the serving runtime (aao_serve.cu) ----
+aao_status aaoi_rebind(aao_handle* h, double tau, double alpha, double c2) {
+  if (!h) return fail(AAO_EINVAL, "null handle");
+  if (!(tau > 0.0) || !(alpha > 0.0 && alpha <= 1.0) || !(c2 > 0.0))
+    return fail(AAO_EINVAL, "bad tau/alpha/c2");
+  AAO_CK(cudaSetDevice(h->device));
+  return set_params(h, tau, alpha, c2, h->cap_stream ? h->cap_stream : (cudaStream_t)0);
+}
+
+// Enqueue one complete FP64 solve (DST of b, the graph-captured MINRES, DST back,
+// physical residual) on stream s without waiting; aaoi_solve_collect reads the result
+// once the stream has reached the end of this work.
+aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double rtol, int maxit,
+                              cudaStream_t s) {
+  if (!h || !b || !x) return fail(AAO_EINVAL, "null pointer");
+  if (h->precision != AAO_PREC_FP64 || h->var_on || !h->use_graph)
+    return fail(AAO_EINVAL, "asynchronous solves need an FP64, constant-coefficient, graph handle");
+  AAO_TRY(dst_apply(h, b, h->vbh, 1, s));
+  MinresCtx c{h, h->vbh, h->vxh, 1, rtol, maxit, s, true, false};
+  cudaGraphExec_t ex = nullptr;
+  AAO_TRY(get_graph(c, 0, &ex));
+  AAO_CK(cudaGraphLaunch(ex, s));
+  AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(MinresScalars), cudaMemcpyDeviceToHost, s));
+  AAO_TRY(dst_apply(h, h->vxh, x, 1, s));
+  double* p1 = h->partial;
+  double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
+  int nb = 0;
+  AAO_CK(launch_op(h, x, nullptr, b, p1, 2, 1, s, &nb));
+  AAO_CK(launch_dot(h->P, b, b, p2, 1, s, &h->launches));
+  AAO_CK(launch_relres(p1, nb, p2, dot_blocks_per_rhs(h->P), h->relres_dev, 1, s, &h->launches));
+  AAO_CK(cudaMemcpyAsync(h->relres_host, h->relres_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return AAO_OK;
+}
+
+aao_status aaoi_solve_collect(aao_handle* h, double rtol, aao_solve_info* info) {
+  aao_status st = minres_collect(h, 1, info);
+  info->relres_true = h->relres_host[0];
+  if (info->relres_true > rtol && info->status == AAO_OK) info->status = AAO_ENOTCONV;
+  if (info->status != AAO_OK && st == AAO_OK) st = (aao_status)info->status;
+  return st;
+}
+
+size_t aaoi_estimate_bytes(int dim, int N, int nt) {
+  size_t m = 1;
+  for (int i = 0; i < dim; ++i) m *= (size_t)N;
+  const size_t npairs = (m + 1) / 2;
+  const size_t vec = (size_t)nt * m * sizeof(double);
+  const size_t nbyt = ((m + 255) / 256) * (((size_t)nt + 31) / 32);
+  return 9 * vec + (size_t)(nt / 2 + 1) * npairs * 2 * sizeof(double2) + m * sizeof(double) +
+         3 * std::max(nbyt, (size_t)296) * sizeof(double) + (1 << 16);
+}
 
 extern "C" {
 
@@ -475,7 +823,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   if (o.nrhs_max < 1) o.nrhs_max = 1;
   if (o.precision != AAO_PREC_FP64 && o.precision != AAO_PREC_FP32_IR)
     return fail(AAO_EINVAL, "unknown precision");
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 4; ++i)
     if (o.reserved[i] != 0) return fail(AAO_EINVAL, "opts.reserved must be zero");
 
   aao_handle* h = new aao_handle();
@@ -495,61 +843,38 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   P.c2 = grid->c2;
   P.h = 1.0 / (double)M;
   P.coef = P.c2 * tau * tau / (2.0 * P.h * P.h);
+  if (const char* tv = getenv("AAO_TIME_VARIANT")) {  // tuning override: "v64,v32"
+    int a = 0, b = -1;
+    if (sscanf(tv, "%d,%d", &a, &b) >= 1) { P.time_variant64 = a & 3; P.time_variant32 = (b >= 0 ? b : a) & 3; }
+  }
+  if (const char* dv = getenv("AAO_DST_VARIANT")) P.dst_variant = atoi(dv) & 1;
 
   auto bail = [&](aao_status st) { delete h; return st; };
 
-  // ---- host tables (long double, rounded) ----
+  // ---- static host tables (long double, rounded): twiddles, DST weights, 1D eigenvalues ----
   const long double pi = 3.141592653589793238462643383279502884L;
-  std::vector<double2> twS, twT, wq(2 * (size_t)nt);
+  std::vector<double2> twS, twT;
   host_twiddles(M, -1, twS);
   host_twiddles(nt, -1, twT);
-  std::vector<double> sinw(M / 2 + 1), dinv(nt), d2(nt), mu(P.N);
+  std::vector<double> sinw(M / 2 + 1), mu(P.N);
   const long double cM = sqrtl(2.0L / (long double)M);
   for (int j = 0; j <= M / 2; ++j) sinw[j] = (double)(cM * sinl(pi * j / (long double)M) / 2.0L);
-  const long double la = logl((long double)alpha);
-  {
-    // per-frequency terms of Sigma = (1 - a theta^k)^2 + (Lambda - 1)(1 + a^2 theta^{2k})
-    const long double a = expl(la / nt), one_minus_a = -expm1l(la / nt);
-    for (int k = 0; k < nt; ++k) {
-      const long double phi = 2.0L * pi * (long double)k / (long double)nt;
-      const long double sh = sinl(phi / 2.0L), c = cosl(phi), sn = sinl(phi);
-      const long double wr = one_minus_a + 2.0L * a * sh * sh, wi = -a * sn;
-      wq[2 * k] = make_double2((double)((wr - wi) * (wr + wi)), (double)(2.0L * wr * wi));
-      const long double qr = one_minus_a * (1.0L + a) + 2.0L * a * a * c * c;
-      wq[2 * k + 1] = make_double2((double)qr, (double)(2.0L * a * a * sn * c));
-    }
-  }
-  for (int t = 0; t < nt; ++t) {
-    dinv[t] = (double)expl(-la * (long double)t / (long double)nt);
-    d2[t] = (double)expl(2.0L * la * (long double)t / (long double)nt);
-  }
   const long double hl = 1.0L / (long double)M;
-  std::vector<long double> mul(P.N);
   for (int i = 0; i < P.N; ++i) {
     const long double sv = sinl((long double)(i + 1) * pi * hl / 2.0L);
-    mul[i] = 4.0L / (hl * hl) * sv * sv;
-    mu[i] = (double)mul[i];
-  }
-  // Lambda_s = 1 + (c2 tau^2/2) sum_axes mu(i_axis), lexicographic s (x fastest)
-  std::vector<double> lam((size_t)P.m);
-  {
-    const long double ct = 0.5L * (long double)grid->c2 * (long double)tau * (long double)tau;
-    for (long long s_ = 0; s_ < P.m; ++s_) {
-      long long rest = s_;
-      long double sum = 0.0L;
-      for (int ax = 0; ax < P.d; ++ax) { sum += mul[rest % P.N]; rest /= P.N; }
-      lam[(size_t)s_] = (double)(1.0L + ct * sum);
-    }
+    mu[i] = (double)(4.0L / (hl * hl) * sv * sv);
   }
 
   // ---- device allocations ----
   aao_status st;
   const size_t tabn = (size_t)(nt / 2 + 1) * P.npairs * 2;
-  double* d_mu = nullptr; double2* d_wq = nullptr; double* d_mm = nullptr;
+  const long long ntab = (long long)(nt / 2 + 1) * P.npairs;
+  h->mm_blocks = (int)((ntab + 255) / 256);
   if ((st = h->alloc(&h->tw_space64, M)) || (st = h->alloc(&h->sinw64, M / 2 + 1)) ||
       (st = h->alloc(&h->tw_time64, nt)) || (st = h->alloc(&h->dinv64, nt)) ||
       (st = h->alloc(&h->d264, nt)) || (st = h->alloc(&h->ab64, tabn)) ||
-      (st = h->alloc(&d_mu, P.N)) || (st = h->alloc(&d_wq, 2 * (size_t)nt)))
+      (st = h->alloc(&h->d_mu, P.N)) || (st = h->alloc(&h->d_wq, 2 * (size_t)nt)) ||
+      (st = h->alloc(&h->d_mm, (size_t)2 * h->mm_blocks)))
     return bail(st);
   const bool fp32 = (o.precision == AAO_PREC_FP32_IR);
   if (fp32) {
@@ -561,9 +886,22 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   const size_t vl = (size_t)h->nrhs_max * (size_t)nt * P.m;
   if ((st = h->alloc(&h->vT, vl)) || (st = h->alloc(&h->vv, vl)) || (st = h->alloc(&h->vvp, vl)) ||
       (st = h->alloc(&h->vz, vl)) || (st = h->alloc(&h->vzn, vl)) || (st = h->alloc(&h->vw, vl)) ||
-      (st = h->alloc(&h->vwp, vl)) || (st = h->alloc(&h->vbh, vl)) ||
+      (st = h->alloc(&h->vwp, vl)) || (st = h->alloc(&h->vbh, vl)) || (st = h->alloc(&h->vxh, vl)) ||
       (st = h->alloc(&h->lam64, (size_t)P.m)) || (st = h->alloc(&h->relres_dev, (size_t)h->nrhs_max)))
     return bail(st);
+  if (o.graph) {
+    h->use_graph = true;
+    if ((st = h->alloc(&h->d_trips, 1))) return bail(st);
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(AAO_ECUDA, "cudaStreamCreate failed"));
+    }
+  }
+  if (o.variable_coefficient) {
+    size_t fsz = (size_t)P.d * (P.N + 1);
+    for (int i = 1; i < P.d; ++i) fsz *= P.N;
+    if ((st = h->alloc(&h->face, fsz))) return bail(st);
+  }
   if (fp32) {
     if ((st = h->alloc(&h->vr, vl)) || (st = h->alloc(&h->vdx, vl)) || (st = h->alloc(&h->f32, vl)))
       return bail(st);
@@ -582,17 +920,11 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     AAO_TRY(upload(twS, h->tw_space64));
     AAO_TRY(upload(sinw, h->sinw64));
     AAO_TRY(upload(twT, h->tw_time64));
-    AAO_TRY(upload(dinv, h->dinv64));
-    AAO_TRY(upload(d2, h->d264));
-    AAO_TRY(upload(mu, d_mu));
-    AAO_TRY(upload(wq, d_wq));
-    AAO_TRY(upload(lam, h->lam64));
+    AAO_TRY(upload(mu, h->d_mu));
     if (fp32) {
       AAO_TRY(upload(to_f2(twS), h->tw_space32));
       AAO_TRY(upload(to_f(sinw), h->sinw32));
       AAO_TRY(upload(to_f2(twT), h->tw_time32));
-      AAO_TRY(upload(to_f(dinv), h->dinv32));
-      AAO_TRY(upload(to_f(d2), h->d232));
     }
     P.t64.tw_space = h->tw_space64; P.t64.sinw = h->sinw64; P.t64.tw_time = h->tw_time64;
     P.t64.dinv = h->dinv64; P.t64.d2 = h->d264; P.t64.ab = h->ab64;
@@ -602,28 +934,26 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
       P.t32.dinv = h->dinv32; P.t32.d2 = h->d232; P.t32.ab = h->ab32;
       P.t32.cq = (float)(cM / 4.0L);
     }
-    const long long total = (long long)(nt / 2 + 1) * P.npairs;
-    const int nbk = (int)((total + 255) / 256);
-    AAO_TRY(h->alloc(&d_mm, (size_t)2 * nbk));
-    int nb = 0;
-    AAO_CK(launch_spectral_table(P, d_mu, d_wq, h->ab64, fp32 ? h->ab32 : nullptr, d_mm, &nb,
-                                 0, &h->launches));
-    std::vector<double> mm((size_t)2 * nb);
-    AAO_CK(cudaMemcpy(mm.data(), d_mm, mm.size() * sizeof(double), cudaMemcpyDeviceToHost));
-    double smin = 1e300, smax = 0.0;
-    for (int i = 0; i < nb; ++i) {
-      smin = std::min(smin, mm[2 * i]);
-      smax = std::max(smax, mm[2 * i + 1]);
-    }
-    if (!(smin > 1e-12 * smax))
-      return fail(AAO_ESINGULAR, "min |Sigma| / max |Sigma| = " + std::to_string(smin / smax) +
-                                     " below 1e-12: preconditioner singular");
+    AAO_TRY(set_params(h, tau, alpha, grid->c2, 0));
     AAO_CK(cudaDeviceSynchronize());
     return AAO_OK;
   };
   st = run();
   if (st != AAO_OK) return bail(st);
   *out = h;
+  return AAO_OK;
+}
+
+aao_status aao_set_coefficient(aao_handle* h, const double* a_face, void* stream) {
+  AAO_TRY(check_handle(h));
+  if (!a_face) return fail(AAO_EINVAL, "null pointer");
+  if (!h->face) return fail(AAO_EINVAL, "handle was created without opts.variable_coefficient");
+  AAO_CK(cudaSetDevice(h->device));
+  size_t fsz = (size_t)h->P.d * (h->P.N + 1);
+  for (int i = 1; i < h->P.d; ++i) fsz *= h->P.N;
+  AAO_CK(cudaMemcpyAsync(h->face, a_face, fsz * sizeof(double), cudaMemcpyDeviceToDevice,
+                         (cudaStream_t)stream));
+  h->var_on = true;
   return AAO_OK;
 }
 
@@ -678,7 +1008,7 @@ aao_status aao_build_rhs(aao_handle* h, const double* f, const double* psi0, con
                          double* b, int nrhs, void* stream) {
   AAO_TRY(check_call(h, nrhs));
   if (!f || !psi0 || !psi1 || !b) return fail(AAO_EINVAL, "null pointer");
-  AAO_KL(h, KC_RHS, (cudaStream_t)stream, launch_build_rhs(h->P, f, psi0, psi1, b, nrhs, (cudaStream_t)stream, &h->launches));
+  AAO_KL(h, KC_RHS, (cudaStream_t)stream, launch_rhs(h, f, psi0, psi1, b, nrhs, (cudaStream_t)stream));
   return AAO_OK;
 }
 
@@ -686,7 +1016,7 @@ aao_status aao_apply_op(aao_handle* h, const double* x, double* y, int nrhs, voi
   AAO_TRY(check_call(h, nrhs));
   if (!x || !y) return fail(AAO_EINVAL, "null pointer");
   if (x == y) return fail(AAO_EINVAL, "x and y must not alias");
-  AAO_KL(h, KC_YT, (cudaStream_t)stream, launch_yt(h->P, x, y, nullptr, nullptr, 0, nrhs, (cudaStream_t)stream, &h->launches, nullptr));
+  AAO_KL(h, KC_YT, (cudaStream_t)stream, launch_op(h, x, y, nullptr, nullptr, 0, nrhs, (cudaStream_t)stream, nullptr));
   return AAO_OK;
 }
 
@@ -732,7 +1062,7 @@ aao_status aao_residual_norm(aao_handle* h, const double* b, const double* x, do
   double* p1 = h->partial;
   double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
   int nb = 0;
-  AAO_KL(h, KC_YT_RES, s, launch_yt(h->P, x, nullptr, b, p1, 2, nrhs, s, &h->launches, &nb));
+  AAO_KL(h, KC_YT_RES, s, launch_op(h, x, nullptr, b, p1, 2, nrhs, s, &nb));
   AAO_KL(h, KC_DOT, s, launch_dot(h->P, b, b, p2, nrhs, s, &h->launches));
   AAO_KL(h, KC_SCAL, s, launch_relres(p1, nb, p2, dot_blocks_per_rhs(h->P), relres, nrhs, s, &h->launches));
   return AAO_OK;
@@ -758,7 +1088,7 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
   AAO_CK(cudaMemcpyAsync(h->hs_f, f, vb, cudaMemcpyHostToDevice, s));
   AAO_CK(cudaMemcpyAsync(d_psi0, psi0, pb, cudaMemcpyHostToDevice, s));
   AAO_CK(cudaMemcpyAsync(d_psi1, psi1, pb, cudaMemcpyHostToDevice, s));
-  AAO_KL(h, KC_RHS, s, launch_build_rhs(h->P, h->hs_f, d_psi0, d_psi1, h->hs_b, nrhs, s, &h->launches));
+  AAO_KL(h, KC_RHS, s, launch_rhs(h, h->hs_f, d_psi0, d_psi1, h->hs_b, nrhs, s));
   aao_status st = aao_minres_solve(h, h->hs_b, h->hs_x, 0, nrhs, rtol, maxit, info, stream);
   if (st != AAO_OK && st != AAO_ENOTCONV && st != AAO_EBREAKDOWN) return st;
   AAO_CK(cudaMemcpyAsync(u, h->hs_x, vb, cudaMemcpyDeviceToHost, s));

@@ -59,6 +59,11 @@ struct Plan {
   int d = 0, N = 0, M = 0, n = 0, m = 0, npairs = 0;
   double tau = 0, alpha = 0, c2 = 0, h = 0;
   double coef = 0;  // c2 tau^2 / (2 h^2): L w = w - coef * (sum of neighbour differences)
+  // time-kernel variant per precision: bit 0 = radix-16 stage plan, bit 1 = half-size tile
+  // (radix-16 + half tile measured fastest on GB300 for both precisions)
+  int time_variant64 = 3, time_variant32 = 3;
+  // DST stage plan: 0 = radix-4, 1 = radix-16 first
+  int dst_variant = 1;
   PrecTables<double> t64;
   PrecTables<float> t32;
 };
@@ -93,6 +98,11 @@ cudaError_t launch_time_mixed(const Plan& P, const double* in, double* out, int 
 
 cudaError_t launch_build_rhs(const Plan& P, const double* f, const double* psi0, const double* psi1,
                              double* b, int nrhs, cudaStream_t s, uint64_t* nl);
+// Variable coefficient (face arrays, see aao_set_coefficient): operator and right-hand side.
+cudaError_t launch_yt_var(const Plan& P, const double* face, const double* x, double* y, const double* w,
+                          double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
+cudaError_t launch_build_rhs_var(const Plan& P, const double* face, const double* f, const double* psi0,
+                                 const double* psi1, double* b, int nrhs, cudaStream_t s, uint64_t* nl);
 
 // Spectral factor table (device), returns min/max |Sigma| per block in mm (host-readable after sync).
 // wq: 2n entries, wq[2k] = (1 - a theta^k)^2, wq[2k+1] = 1 + a^2 theta^{2k}.
@@ -129,6 +139,9 @@ cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* 
 cudaError_t launch_scalars(int step, MinresScalars* sc, const double* partial, int nb,
                            const double* partial2, int nb2, const double* partial3, int nb3,
                            int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl);
+// Graph WHILE-loop control: trips += count; condition = (any rhs not done) && trips < limit.
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle hw, const MinresScalars* sc, int nrhs, int* trips,
+                             int trip_limit, int count, cudaStream_t s, uint64_t* nl);
 // relres[r] = sqrt(sum of p1 partials / sum of p2 partials) per right-hand side
 cudaError_t launch_relres(const double* p1, int nb1, const double* p2, int nb2, double* relres,
                           int nrhs, cudaStream_t s, uint64_t* nl);
@@ -138,3 +151,10 @@ cudaError_t launch_axpy(double a, const double* x, double* y, size_t count, cuda
                         uint64_t* nl);
 
 }  // namespace aao
+
+// Handle-level internals used by the serving runtime (defined in aao_api.cu).
+aao_status aaoi_rebind(aao_handle* h, double tau, double alpha, double c2);
+aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double rtol, int maxit,
+                              cudaStream_t s);
+aao_status aaoi_solve_collect(aao_handle* h, double rtol, aao_solve_info* info);
+size_t aaoi_estimate_bytes(int dim, int N, int nt);

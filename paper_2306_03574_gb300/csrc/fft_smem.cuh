@@ -116,4 +116,145 @@ __device__ __forceinline__ void fft_block(C* buf, const C* tw) {
   if constexpr ((LG & 1) != 0) fft_stage2_last<L, NS, NT, INV>(buf, tw);
 }
 
+// ---------------------------------------------------------------------------
+// Higher radices: in-register 8- and 16-point DFTs and a generic radix-RX
+// Stockham stage.  Fewer stages mean fewer shared-memory round trips and
+// barriers; the internal twiddles of the 16-point DFT are the constants
+// exp(-+ 2 pi i m / 16).
+// ---------------------------------------------------------------------------
+
+// v * exp(-+ 2 pi i m / 16) for the constant m (INV: the conjugate root)
+template <int M, bool INV, typename C>
+AAO_HD C w16(C v) {
+  using R = decltype(v.x);
+  constexpr double c1 = 0.92387953251128675613;  // cos(pi/8)
+  constexpr double s1 = 0.38268343236508977173;  // sin(pi/8)
+  constexpr double h = 0.70710678118654752440;   // sqrt(2)/2
+  constexpr int m = M & 15;
+  double cr, ci;  // exp(-2 pi i m/16) = cos - i sin
+  switch (m) {
+    case 0: return v;
+    case 1: cr = c1; ci = -s1; break;
+    case 2: cr = h; ci = -h; break;
+    case 3: cr = s1; ci = -c1; break;
+    case 4: { C o; if (!INV) { o.x = v.y; o.y = -v.x; } else { o.x = -v.y; o.y = v.x; } return o; }
+    case 5: cr = -s1; ci = -c1; break;
+    case 6: cr = -h; ci = -h; break;
+    case 7: cr = -c1; ci = -s1; break;
+    case 8: { C o; o.x = -v.x; o.y = -v.y; return o; }
+    case 9: cr = -c1; ci = s1; break;
+    default: cr = 0; ci = 0; break;
+  }
+  if (INV) ci = -ci;
+  C w; w.x = R(cr); w.y = R(ci);
+  return cmul(v, w);
+}
+
+template <bool INV, typename C>
+AAO_HD void dft8(C* v) {
+  // radix-2 over even/odd inputs: X_k = E_k + W8^k O_k, X_{k+4} = E_k - W8^k O_k
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  o1 = w16<2, INV>(o1);
+  o2 = w16<4, INV>(o2);
+  o3 = w16<6, INV>(o3);
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+template <bool INV, typename C>
+AAO_HD void dft16(C* v) {
+  // 16 = 4 x 4: DFT4 over n1 (stride 4) for each n2, twiddle W16^{n2 k1}, DFT4 over n2;
+  // X[k1 + 4 k2] = sum_n2 W4^{n2 k2} W16^{n2 k1} sum_n1 x[4 n1 + n2] W4^{n1 k1}
+  C a[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C x0 = v[n2], x1 = v[4 + n2], x2 = v[8 + n2], x3 = v[12 + n2];
+    dft4<INV>(x0, x1, x2, x3);
+    a[4 * n2 + 0] = x0; a[4 * n2 + 1] = x1; a[4 * n2 + 2] = x2; a[4 * n2 + 3] = x3;
+  }
+  a[5] = w16<1, INV>(a[5]);   a[6] = w16<2, INV>(a[6]);   a[7] = w16<3, INV>(a[7]);
+  a[9] = w16<2, INV>(a[9]);   a[10] = w16<4, INV>(a[10]); a[11] = w16<6, INV>(a[11]);
+  a[13] = w16<3, INV>(a[13]); a[14] = w16<6, INV>(a[14]); a[15] = w16<9, INV>(a[15]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C y0 = a[k1], y1 = a[4 + k1], y2 = a[8 + k1], y3 = a[12 + k1];
+    dft4<INV>(y0, y1, y2, y3);
+    v[k1] = y0; v[k1 + 4] = y1; v[k1 + 8] = y2; v[k1 + 12] = y3;
+  }
+}
+
+template <int RX, bool INV, typename C>
+AAO_HD void dft_r(C* v) {
+  if constexpr (RX == 2) { C a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
+  else if constexpr (RX == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (RX == 8) dft8<INV>(v);
+  else dft16<INV>(v);
+}
+
+// One radix-RX Stockham stage with span Ls (sub-transforms of length Ls done):
+// task j in [0, L/RX), k = j mod Ls, v_r = x[j + r L/RX], v_r *= w^{r k L/(RX Ls)},
+// DFT_RX, y[(j - k) RX + k + r Ls] = v_r.
+template <int L, int NS, int NT, int RX, bool INV, typename C>
+__device__ __forceinline__ void fft_stage_r(C* buf, const C* tw, int Ls) {
+  constexpr int Q = L / RX;
+  constexpr int TASKS = NS * Q;
+  static_assert(TASKS % NT == 0, "radix tasks must divide evenly among threads");
+  constexpr int TPT = TASKS / NT;
+  C v[TPT][RX];
+#pragma unroll
+  for (int t = 0; t < TPT; ++t) {
+    const int task = threadIdx.x + t * NT;
+    const int q = task / Q, j = task % Q;
+    const C* p = buf + q * L + j;
+#pragma unroll
+    for (int r = 0; r < RX; ++r) v[t][r] = p[r * Q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < TPT; ++t) {
+    const int task = threadIdx.x + t * NT;
+    const int q = task / Q, j = task % Q;
+    const int k = j & (Ls - 1);
+    if (Ls > 1) {
+      const int step = (Q / Ls) * k;
+#pragma unroll
+      for (int r = 1; r < RX; ++r) v[t][r] = cmul(v[t][r], twid<INV>(tw[r * step]));
+    }
+    dft_r<RX, INV>(v[t]);
+    C* o = buf + q * L + (j - k) * RX + k;
+#pragma unroll
+    for (int r = 0; r < RX; ++r) o[r * Ls] = v[t][r];
+  }
+  __syncthreads();
+}
+
+// Stage plans with radix-16 first: 64 = 16*4, 128 = 16*8, 256 = 16*16,
+// 512 = 16*16*2, 1024 = 16*16*4.
+template <int L, int NS, int NT, bool INV, typename C>
+__device__ __forceinline__ void fft_block16(C* buf, const C* tw) {
+  if constexpr (L == 64) {
+    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 4, INV>(buf, tw, 16);
+  } else if constexpr (L == 128) {
+    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 8, INV>(buf, tw, 16);
+  } else if constexpr (L == 256) {
+    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 16);
+  } else if constexpr (L == 512) {
+    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 2, INV>(buf, tw, 256);
+  } else {
+    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 4, INV>(buf, tw, 256);
+  }
+}
+
 }  // namespace aao

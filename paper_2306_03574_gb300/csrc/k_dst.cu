@@ -26,7 +26,7 @@ struct DstArgs {
   long long nouter; // strided axis: number of outer blocks
 };
 
-template <typename R, int M, int NS, int NT, bool STRIDED>
+template <typename R, int M, int NS, int NT, bool STRIDED, int FFTV>
 __global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
   constexpr int H = M / 2;
@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, Prec
   for (int q = tid; q < NS; q += NT) { C z; z.x = 0; z.y = 0; cbuf[q * M] = z; }
   __syncthreads();
 
-  fft_block<M, NS, NT, false>(cbuf, tw);
+  if constexpr (FFTV == 0) fft_block<M, NS, NT, false>(cbuf, tw);
+  else fft_block16<M, NS, NT, false>(cbuf, tw);
 
   // ---- post-processing: separate the two lines, prefix sum for odd outputs ----
   const int q = tid / TPS, lq = tid % TPS;
@@ -167,9 +168,9 @@ __global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, Prec
   }
 }
 
-template <typename R, int M>
-static cudaError_t dst_launch_M(const Plan& P, const R* in, R* out, int axis, int nrhs,
-                                cudaStream_t s) {
+template <typename R, int M, int FFTV>
+static cudaError_t dst_launch_MV(const Plan& P, const R* in, R* out, int axis, int nrhs,
+                                 cudaStream_t s) {
   using C = typename Cplx<R>::T;
   constexpr int NT = 128;
   constexpr int NS = 2048 / M;
@@ -184,7 +185,7 @@ static cudaError_t dst_launch_M(const Plan& P, const R* in, R* out, int axis, in
     a.nlines = total / P.N;
     a.st = 1;
     a.nouter = 0;
-    auto kern = k_dst<R, M, NS, NT, false>;
+    auto kern = k_dst<R, M, NS, NT, false, FFTV>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const long long nb = (a.nlines + 2 * NS - 1) / (2 * NS);
     kern<<<dim3((unsigned)nb), NT, smem, s>>>(in, out, a, tb);
@@ -192,12 +193,19 @@ static cudaError_t dst_launch_M(const Plan& P, const R* in, R* out, int axis, in
     a.st = (int)stride;
     a.nouter = total / (stride * P.N);
     a.nlines = 0;
-    auto kern = k_dst<R, M, NS, NT, true>;
+    auto kern = k_dst<R, M, NS, NT, true, FFTV>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int ntile = (int)((stride + 2 * NS - 1) / (2 * NS));
     kern<<<dim3((unsigned)a.nouter, (unsigned)ntile), NT, smem, s>>>(in, out, a, tb);
   }
   return cudaGetLastError();
+}
+
+template <typename R, int M>
+static cudaError_t dst_launch_M(const Plan& P, const R* in, R* out, int axis, int nrhs,
+                                cudaStream_t s) {
+  return P.dst_variant ? dst_launch_MV<R, M, 1>(P, in, out, axis, nrhs, s)
+                       : dst_launch_MV<R, M, 0>(P, in, out, axis, nrhs, s);
 }
 
 template <typename R>

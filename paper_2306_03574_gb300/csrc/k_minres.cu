@@ -213,6 +213,20 @@ __global__ void k_relres(const double* __restrict__ p1, int nb1, const double* _
   if (threadIdx.x == 0) relres[r] = (s2 > 0.0) ? sqrt(s1 / s2) : sqrt(s1);
 }
 
+// Device-side loop control for the graph-captured solve: counts the trip and sets
+// the WHILE condition to "some right-hand side still iterating and trips < limit"
+// (the limit bounds the loop whatever the scalar state holds).
+__global__ void k_loop_cond(cudaGraphConditionalHandle hw, const MinresScalars* __restrict__ sc, int nrhs,
+                            int* trips, int trip_limit, int count) {
+  if (threadIdx.x != 0) return;
+  const int t = *trips + count;
+  *trips = t;
+  bool any = false;
+  for (int r = 0; r < nrhs; ++r)
+    if (!sc[r].done) any = true;
+  cudaGraphSetConditional(hw, (any && t < trip_limit) ? 1u : 0u);
+}
+
 inline dim3 vgrid(const Plan& P, int nrhs) {
   const long long len = (long long)P.n * P.m;
   long long b = (len + VNT - 1) / VNT;
@@ -253,6 +267,13 @@ cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* 
   long long nb = (len + VNT - 1) / VNT;
   if (nb > 152 * 8) nb = 152 * 8;
   k_sub<<<(unsigned)nb, VNT, 0, s>>>(a, b, y, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_cond(cudaGraphConditionalHandle hw, const MinresScalars* sc, int nrhs, int* trips,
+                             int trip_limit, int count, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  k_loop_cond<<<1, 32, 0, s>>>(hw, sc, nrhs, trips, trip_limit, count);
   return cudaGetLastError();
 }
 

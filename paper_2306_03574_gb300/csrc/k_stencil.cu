@@ -135,6 +135,115 @@ __global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, d
   }
 }
 
+// Variable coefficient: L_a w(s) = w(s) + cv sum_axes [aR (w(s) - w(s+e)) + aL (w(s) - w(s-e))],
+// cv = tau^2/(2h^2), aR/aL the coefficients on the faces right/left of s along the axis
+// (face arrays concatenated by axis; axis ax has N+1 faces along ax, N along the others).
+struct VarArgs {
+  int N, n, m, d;
+  double cv;
+  const double* face;  // d * (N+1) * N^(d-1)
+};
+
+template <int D>
+__device__ __forceinline__ double apply_La(const double* __restrict__ v, int s, int ix, int iy, int iz,
+                                           const VarArgs& a) {
+  const int N = a.N;
+  const long long fsz = (long long)(N + 1) * (D == 1 ? 1 : (D == 2 ? N : N * N));
+  const double c = v[s];
+  double acc;
+  {  // x faces: index (iz*N + iy)*(N+1) + f
+    const double* F = a.face;
+    const long long base = ((long long)iz * N + iy) * (N + 1);
+    const double aL = F[base + ix], aR = F[base + ix + 1];
+    const double wl = ix > 0 ? v[s - 1] : 0.0, wr = ix < N - 1 ? v[s + 1] : 0.0;
+    acc = fma(aR, c - wr, aL * (c - wl));
+  }
+  if (D >= 2) {  // y faces: index (iz*(N+1) + f)*N + ix
+    const double* F = a.face + fsz;
+    const long long base = (long long)iz * (N + 1);
+    const double aL = F[(base + iy) * N + ix], aR = F[(base + iy + 1) * N + ix];
+    const double wl = iy > 0 ? v[s - N] : 0.0, wr = iy < N - 1 ? v[s + N] : 0.0;
+    acc = fma(aR, c - wr, fma(aL, c - wl, acc));
+  }
+  if (D >= 3) {  // z faces: index (f*N + iy)*N + ix
+    const double* F = a.face + 2 * fsz;
+    const double aL = F[((long long)iz * N + iy) * N + ix], aR = F[((long long)(iz + 1) * N + iy) * N + ix];
+    const double wl = iz > 0 ? v[s - N * N] : 0.0, wr = iz < N - 1 ? v[s + N * N] : 0.0;
+    acc = fma(aR, c - wr, fma(aL, c - wl, acc));
+  }
+  return fma(a.cv, acc, c);
+}
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(YT_NT) k_yt_var(const double* __restrict__ x, double* __restrict__ y,
+                                                  const double* __restrict__ w,
+                                                  double* __restrict__ partial, VarArgs a) {
+  const int s = blockIdx.x * YT_NT + threadIdx.x;
+  const int n = a.n, m = a.m, N = a.N;
+  const int i0 = blockIdx.y * YT_CH;
+  const int i1 = min(n, i0 + YT_CH);
+  const long long rb = (long long)blockIdx.z * n * m;
+  double acc = 0.0;
+  if (s < m) {
+    const int ix = s % N;
+    const int iy = (D >= 2) ? (s / N) % N : 0;
+    const int iz = (D >= 3) ? s / (N * N) : 0;
+    const double* xr = x + rb;
+    double Lv1 = 0.0, Lv2 = 0.0, v1 = 0.0;
+    for (int i = max(0, i0 - 2); i < i1; ++i) {
+      const double* vi = xr + (long long)i * m;
+      const double Lv = apply_La<D>(vi, s, ix, iy, iz, a);
+      if (i >= i0) {
+        const double o = fma(-2.0, v1, Lv + Lv2);
+        const long long idx = rb + (long long)(n - 1 - i) * m + s;
+        if (MODE != 2) y[idx] = o;
+        if (MODE == 1) acc = fma(o, w[idx], acc);
+        if (MODE == 2) {
+          const double r = w[idx] - o;
+          acc = fma(r, r, acc);
+        }
+      }
+      Lv2 = Lv1;
+      Lv1 = Lv;
+      v1 = vi[s];
+    }
+  }
+  if (MODE != 0) {
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) {
+      const long long nb = (long long)gridDim.x * gridDim.y;
+      partial[blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(YT_NT) k_rhs_var(const double* __restrict__ f,
+                                                   const double* __restrict__ psi0,
+                                                   const double* __restrict__ psi1,
+                                                   double* __restrict__ b, VarArgs a, double tau) {
+  const int s = blockIdx.x * YT_NT + threadIdx.x;
+  const int k = blockIdx.y;
+  const int n = a.n, m = a.m, N = a.N;
+  if (s >= m) return;
+  const long long rb = (long long)blockIdx.z * n * m;
+  const long long ib = (long long)blockIdx.z * m;
+  const double t2 = tau * tau;
+  const double fk = f[rb + (long long)k * m + s];
+  double v;
+  if (k == 0) {
+    v = fma(0.5 * t2, fk, fma(tau, psi1[ib + s], psi0[ib + s]));
+  } else if (k == 1) {
+    const int ix = s % N;
+    const int iy = (D >= 2) ? (s / N) % N : 0;
+    const int iz = (D >= 3) ? s / (N * N) : 0;
+    v = fma(t2, fk, -apply_La<D>(psi0 + ib, s, ix, iy, iz, a));
+  } else {
+    v = t2 * fk;
+  }
+  b[rb + (long long)(n - 1 - k) * m + s] = v;
+}
+
 // b[n-1-k] = tau^2 f^k for k >= 2; tau^2 f^1 - L psi0; tau^2 f^0/2 + tau psi1 + psi0.
 template <int D>
 __global__ void __launch_bounds__(YT_NT) k_rhs(const double* __restrict__ f,
@@ -211,6 +320,54 @@ cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, doub
   if (mode == 0) k_ythat<0><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
   else if (mode == 1) k_ythat<1><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
   else k_ythat<2><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
+  return cudaGetLastError();
+}
+
+static VarArgs make_var(const Plan& P, const double* face) {
+  VarArgs a;
+  a.N = P.N;
+  a.n = P.n;
+  a.m = P.m;
+  a.d = P.d;
+  a.cv = P.tau * P.tau / (2.0 * P.h * P.h);
+  a.face = face;
+  return a;
+}
+
+template <int D>
+static void ytv_dispatch(int mode, dim3 g, cudaStream_t s, const double* x, double* y,
+                         const double* w, double* partial, const VarArgs& a) {
+  if (mode == 0) k_yt_var<D, 0><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
+  else if (mode == 1) k_yt_var<D, 1><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
+  else k_yt_var<D, 2><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
+}
+
+cudaError_t launch_yt_var(const Plan& P, const double* face, const double* x, double* y, const double* w,
+                          double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb) {
+  if (nl) ++*nl;
+  const VarArgs a = make_var(P, face);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
+  if (nb) *nb = (int)(g.x * g.y);
+  switch (P.d) {
+    case 1: ytv_dispatch<1>(mode, g, s, x, y, w, partial, a); break;
+    case 2: ytv_dispatch<2>(mode, g, s, x, y, w, partial, a); break;
+    case 3: ytv_dispatch<3>(mode, g, s, x, y, w, partial, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_rhs_var(const Plan& P, const double* face, const double* f, const double* psi0,
+                                 const double* psi1, double* b, int nrhs, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  const VarArgs a = make_var(P, face);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, P.n, nrhs);
+  switch (P.d) {
+    case 1: k_rhs_var<1><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
+    case 2: k_rhs_var<2><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
+    case 3: k_rhs_var<3><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -14,6 +14,8 @@
 // G_{n-k} = conj(G_k) gives A_{n-k} = conj(A_k), B_{n-k} = conj(B_k), so the
 // table holds k = 0..n/2 only.  A CTA owns 2*NS consecutive modes, all n time
 // levels of them staged in shared memory (coalesced rows of the time-major vector).
+#include <type_traits>
+
 #include "aao_internal.cuh"
 #include "fft_smem.cuh"
 
@@ -59,7 +61,14 @@ __device__ __forceinline__ void mix_pass(C* cbuf, const C* __restrict__ ab, int 
   __syncthreads();
 }
 
-template <typename R, typename TIO, int L, int NS, int NT>
+// FFT stage plan: 0 = radix-4 stages (+ one radix-2), 1 = radix-16 first (fewer passes)
+template <int FFTV, int L, int NS, int NT, bool INV, typename C>
+__device__ __forceinline__ void fft_run(C* buf, const C* tw) {
+  if constexpr (FFTV == 0) fft_block<L, NS, NT, INV>(buf, tw);
+  else fft_block16<L, NS, NT, INV>(buf, tw);
+}
+
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -93,9 +102,9 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
   __syncthreads();
 
   const int p0 = blockIdx.x * NS;
-  fft_block<L, NS, NT, false>(cbuf, tw);
+  fft_run<FFTV, L, NS, NT, false>(cbuf, tw);
   mix_pass<false, L, NS, NT>(cbuf, tb.ab, a.npairs, p0);
-  fft_block<L, NS, NT, true>(cbuf, tw);
+  fft_run<FFTV, L, NS, NT, true>(cbuf, tw);
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
     C z = cbuf[q * L + t];
@@ -104,9 +113,9 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
     cbuf[q * L + t] = z;
   }
   __syncthreads();
-  fft_block<L, NS, NT, false>(cbuf, tw);
+  fft_run<FFTV, L, NS, NT, false>(cbuf, tw);
   mix_pass<true, L, NS, NT>(cbuf, tb.ab, a.npairs, p0);
-  fft_block<L, NS, NT, true>(cbuf, tw);
+  fft_run<FFTV, L, NS, NT, true>(cbuf, tw);
 
   // scale by D^{-1} and store
   for (int task = tid; task < NS * L; task += NT) {
@@ -120,21 +129,31 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
   }
 }
 
-template <typename R, typename TIO, int L>
-static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
+// Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV>
+static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
-  constexpr int NT = 256;
-  constexpr int NS = 4096 / L;
   const size_t smem = sizeof(C) * (NS * L + L) + 2 * sizeof(R) * L;
   TimeArgs a;
   a.m = P.m;
   a.n = P.n;
   a.npairs = P.npairs;
-  auto kern = k_time<R, TIO, L, NS, NT>;
+  auto kern = k_time<R, TIO, L, NS, NT, FFTV>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
   kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
   return cudaGetLastError();
+}
+
+template <typename R, typename TIO, int L>
+static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
+  const int v = std::is_same<R, double>::value ? P.time_variant64 : P.time_variant32;
+  switch (v & 3) {
+    case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0>(P, in, out, nrhs, s);
+    case 1: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1>(P, in, out, nrhs, s);
+    case 2: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 0>(P, in, out, nrhs, s);
+    default: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1>(P, in, out, nrhs, s);
+  }
 }
 
 template <typename R, typename TIO>

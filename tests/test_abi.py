@@ -47,6 +47,7 @@ def test_status_strings(L):
 ])
 def test_create_rejects_bad_arguments(L, kw, status):
     args = dict(dim=2, N=63, nt=64, tau=1 / 64, alpha=1e-2, c2=1.0, precision=0, nrhs_max=1, scheme=0)
+    args.setdefault("variable_coefficient", False)
     args.update(kw)
     st, h = aao.aao_create(raw_status=True, **args)
     assert st == status, (st, aao.aao_last_error())
@@ -62,3 +63,16 @@ def test_null_pointers_rejected(L):
     assert L.aao_launch_count(None) == 0
     assert L.aao_apply_prec(None, None, None, 1, None) == aao.AAO_EINVAL
     assert L.aao_minres_solve(None, None, None, 0, 1, 1e-8, 10, None, None) == aao.AAO_EINVAL
+
+
+def test_serve_argument_validation(L):
+    """Serving entry points reject bad arguments before touching the GPU."""
+    st, srv = aao.aao_serve_create(0, 4, raw_status=True)
+    assert st == aao.AAO_EINVAL and srv is None
+    st, srv = aao.aao_serve_create(1 << 30, 0, raw_status=True)
+    assert st == aao.AAO_EINVAL
+    st, srv = aao.aao_serve_create(1 << 30, 65, raw_status=True)
+    assert st == aao.AAO_EINVAL
+    assert L.aao_serve_submit(None, None, None) == aao.AAO_EINVAL
+    assert L.aao_serve_poll(None, 1, None) == aao.AAO_EINVAL
+    assert L.aao_serve_destroy(None) == aao.AAO_OK

@@ -1,0 +1,77 @@
+"""Graph-captured solves (device-side WHILE loop) give bit-identical results to the
+host-driven loop: same kernels in the same order on the same buffers."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import system as OS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2306_03574_gb300 as aao  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2306_03574_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    aao.lib()
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("d,N,nt,nrhs,prec,alpha", [
+    (1, 63, 64, 1, 0, 1e-6), (2, 63, 64, 3, 0, 1e-6), (2, 127, 128, 1, 1, 1e-3), (3, 63, 64, 2, 0, 1e-2),
+    (1, 255, 1024, 1, 1, 1e-3),
+])
+def test_graph_equals_host_loop(d, N, nt, nrhs, prec, alpha):
+    m = N ** d
+    tau = 1.0 / nt
+    x = W.random_field((nrhs, nt, m), seed=1400 + N)
+    out = []
+    for graph in (False, True):
+        with aao.Solver(d, N, nt, tau, alpha, precision=prec, nrhs_max=nrhs, graph=graph) as s:
+            xt = cu(x)
+            b = torch.empty_like(xt)
+            s.apply_op(xt, b)
+            res = []
+            for _ in range(2):  # second call reuses the captured graph
+                y = torch.empty_like(xt)
+                st, info = s.solve(b, y, rtol=1e-10, maxit=100)
+                torch.cuda.synchronize()
+                res.append((st, [i["iters"] for i in info], y.cpu().numpy()))
+            out.append(res)
+    (st0, it0, y0), (st0b, it0b, y0b) = out[0]
+    for st, it, y in out[1]:
+        assert st == st0 == aao.AAO_OK
+        assert it == it0
+        assert np.array_equal(y, y0)
+    assert np.abs(y0 - x).max() / np.abs(x).max() < 1e-7
+
+
+def test_graph_variable_coefficient_and_maxit():
+    p = W.example2(63, 64)
+    faces = W.face_coefficients(p.meta["a"], 2, 63)
+    flat = np.concatenate([f.ravel() for f in faces])
+    abar = W.grid_mean(p.meta["a"], 2, 63)
+    b = OS.rhs_b_var(p, faces)
+    got = []
+    for graph in (False, True):
+        with aao.Solver(2, 63, 64, p.tau, 1e-6, c2=abar, variable_coefficient=True, graph=graph) as s:
+            s.set_coefficient(cu(flat))
+            bt = cu(b)
+            y = torch.empty_like(bt)
+            st, info = s.solve(bt, y, rtol=1e-9, maxit=100)
+            y2 = torch.empty_like(bt)
+            st2, info2 = s.solve(bt, y2, rtol=1e-14, maxit=3)   # stops at maxit
+            torch.cuda.synchronize()
+            got.append((st, info[0]["iters"], y.cpu().numpy(), st2, info2[0]["iters"]))
+    assert got[0][0] == got[1][0] == aao.AAO_OK
+    assert got[0][1] == got[1][1]
+    assert np.array_equal(got[0][2], got[1][2])
+    assert got[0][3] == got[1][3] == aao.AAO_ENOTCONV
+    assert got[0][4] == got[1][4] == 3

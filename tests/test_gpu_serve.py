@@ -1,0 +1,118 @@
+"""Serving: requests of mixed sizes, wave speeds, alpha and tolerances admitted onto
+the GPU concurrently under an HBM budget; each result is bit-for-bit the result of
+the same solve run alone; budget eviction, an oversize request, bounded waits."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import system as OS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2306_03574_gb300 as aao  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2306_03574_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    aao.lib()
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _requests(k=24, seed=77):
+    reqs = W.served_requests(count=k, rate=1e9, seed=seed, max_2d_N=127, max_1d_nt=512, max_2d_nt=128)
+    out = []
+    for r in reqs:
+        p = W.served_problem(r, alpha=1e-6)
+        out.append((r, p, cu(p.f), cu(p.psi0), cu(p.psi1), torch.empty((p.nt, p.m), dtype=torch.float64,
+                                                                       device="cuda")))
+    return out
+
+
+def _solo(p, rtol):
+    with aao.Solver(p.d, p.N, p.nt, p.tau, p.alpha, c2=p.c2, graph=True) as s:
+        b = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
+        s.build_rhs(cu(p.f), cu(p.psi0), cu(p.psi1), b)
+        x = torch.empty_like(b)
+        st, info = s.solve(b, x, rtol=rtol, maxit=100)
+        torch.cuda.synchronize()
+        return st, info[0], x.cpu().numpy()
+
+
+def test_mixed_requests_equal_solo_solves():
+    reqs = _requests()
+    srv = aao.aao_serve_create(8 << 30, 6)
+    try:
+        tickets = [aao.aao_serve_submit(srv, p.d, p.N, p.nt, p.tau, p.alpha, p.c2, r["tol"], 100, f, p0, p1, x)
+                   for (r, p, f, p0, p1, x) in reqs]
+        results = []
+        for t in tickets:
+            st, res = aao.aao_serve_wait(srv, t, 120.0)
+            assert st == aao.AAO_OK, (st, res)
+            results.append(res)
+        stats = aao.aao_serve_stats(srv)
+    finally:
+        aao.aao_serve_destroy(srv)
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    assert stats["peak_pool_bytes"] <= stats["budget"]
+    for (r, p, f, p0, p1, x), res in zip(reqs, results):
+        st, info, xs = _solo(p, r["tol"])
+        assert st == aao.AAO_OK
+        assert res["iters"] == info["iters"]
+        assert np.array_equal(x.cpu().numpy(), xs)
+        b = OS.rhs_b(p)
+        rel = np.linalg.norm(b - OS.apply_YT(xs, p.d, p.N, p.tau, p.c2)) / np.linalg.norm(b)
+        assert rel <= r["tol"] * 1.001
+        assert res["t_submit"] <= res["t_start"] <= res["t_done"]
+
+
+def test_budget_eviction_and_oversize():
+    reqs = _requests(k=10, seed=78)
+    one = max(10 * p.nt * p.m * 8 for (_, p, *_rest) in reqs)
+    srv = aao.aao_serve_create(int(2.5 * one), 2)
+    try:
+        tickets = [aao.aao_serve_submit(srv, p.d, p.N, p.nt, p.tau, p.alpha, p.c2, r["tol"], 100, f, p0, p1, x)
+                   for (r, p, f, p0, p1, x) in reqs]
+        for t in tickets:
+            st, res = aao.aao_serve_wait(srv, t, 120.0)
+            assert st == aao.AAO_OK
+        stats = aao.aao_serve_stats(srv)
+        assert stats["peak_pool_bytes"] <= stats["budget"]
+        # a request that can never fit completes with AAO_ENOMEM
+        p = W.config_2d(N=255, nt=512, alpha=1e-6)
+        f, p0, p1 = cu(p.f), cu(p.psi0), cu(p.psi1)
+        x = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
+        t = aao.aao_serve_submit(srv, 2, 255, 512, p.tau, 1e-6, 1.0, 1e-8, 50, f, p0, p1, x)
+        st, res = aao.aao_serve_wait(srv, t, 60.0)
+        assert st == aao.AAO_ENOMEM
+        # unknown ticket
+        assert aao.aao_serve_poll(srv, 123456789)[0] == aao.AAO_EINVAL
+    finally:
+        aao.aao_serve_destroy(srv)
+    assert stats["evictions"] >= 1
+
+
+def test_bounded_wait_times_out_then_completes():
+    p = W.config_2d(N=255, nt=256, alpha=1e-6)
+    f, p0, p1 = cu(p.f), cu(p.psi0), cu(p.psi1)
+    x = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
+    srv = aao.aao_serve_create(8 << 30, 2)
+    try:
+        t = aao.aao_serve_submit(srv, 2, 255, 256, p.tau, 1e-6, 1.0, 1e-8, 100, f, p0, p1, x)
+        st, _ = aao.aao_serve_wait(srv, t, 1e-6)
+        assert st == aao.AAO_ETIMEOUT
+        st, _ = aao.aao_serve_poll(srv, t)
+        assert st in (aao.AAO_EPENDING, aao.AAO_OK)
+        if st == aao.AAO_EPENDING:
+            st, res = aao.aao_serve_wait(srv, t, 120.0)
+            assert st == aao.AAO_OK
+    finally:
+        aao.aao_serve_destroy(srv)

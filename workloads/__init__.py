@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "WaveProblem", "grid_axes", "make_rng", "random_field",
     "config_1d", "config_2d", "config_2d_large", "config_3d_batched",
-    "example1", "example2", "served_requests",
+    "example1", "example2", "served_requests", "face_coefficients", "grid_mean",
 ]
 
 
@@ -182,6 +182,27 @@ def example2(N: int, nt: int, alpha: float = 1e-6) -> WaveProblem:
     afun = lambda X, Y: (30.0 + np.sin(X) ** 2) * (30.0 + np.sin(Y) ** 2)
     return WaveProblem(2, N, nt, 1.0, 1.0, alpha, psi0, psi1, f, exact,
                        name=f"example2_N{N}_nt{nt}", meta={"a": afun})
+
+
+def face_coefficients(afun, d: int, N: int):
+    """A coefficient function sampled on the cell faces: for axis ax (0 = x) an array of
+    shape (N,)*d with axis ax extended to N+1 faces, face f at coordinate (f + 1/2) h
+    along ax (f = 0..N) and grid-point coordinates along the other axes (array axis 0
+    is the slowest coordinate).  afun takes coordinate arrays (x, y, ...)."""
+    h = 1.0 / (N + 1)
+    g = np.arange(1, N + 1) * h
+    fg = (np.arange(N + 1) + 0.5) * h
+    out = []
+    for ax in range(d):
+        axes = [fg if (d - 1 - a) == ax else g for a in range(d)]
+        mesh = np.meshgrid(*axes, indexing="ij")
+        out.append(afun(*[mesh[d - 1 - c] for c in range(d)]))
+    return out
+
+
+def grid_mean(afun, d: int, N: int) -> float:
+    """Mean of a coefficient function over the grid points."""
+    return float(np.mean(afun(*grid_axes(d, N))))
 
 
 def served_requests(count: int = 2000, rate: float = 200.0, seed: int = 5,
