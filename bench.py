@@ -402,25 +402,28 @@ def run_gpu(args, world, rank, local):
     prec["frac_of_8tbs"] = prec["hbm_gbs"] / 8000.0 if prec["hbm_gbs"] else None
 
     # ---- end to end through the C ABI with host buffers ----
-    fh = torch.from_numpy(fnp).pin_memory()
-    p0h = torch.from_numpy(p0np).pin_memory()
-    p1h = torch.from_numpy(p1np).pin_memory()
-    uh = torch.empty((nrhs, p.nt, p.m), dtype=torch.float64).pin_memory()
-    s.solve_host(fh, p0h, p1h, uh, rtol=rtol, maxit=maxit, stream=stream)  # staging warm-up
-    e2e_steps = max(1, min(args.steps, 20))
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        st, inf2 = s.solve_host(fh, p0h, p1h, uh, rtol=rtol, maxit=maxit, stream=stream)
-        if st != aao.AAO_OK:
-            raise RuntimeError(f"host solve failed {inf2}")
-    torch.cuda.synchronize(dev)
-    t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
-    barrier(world)
-    e2e = {"value": world * e2e_steps * nrhs / t_e2e, "unit": "solves/s",
-           "h2d_bytes_per_step": 8 * nrhs * (p.nt * p.m + 2 * p.m), "d2h_bytes_per_step": 8 * nrhs * p.nt * p.m,
-           "steps": e2e_steps, "api": "aao_solve_host"}
+    if unknowns * 8 > 4e9:  # would pin more than 3 x 4 GB of host memory: not measured
+        e2e = None
+    else:
+        fh = torch.from_numpy(fnp).pin_memory()
+        p0h = torch.from_numpy(p0np).pin_memory()
+        p1h = torch.from_numpy(p1np).pin_memory()
+        uh = torch.empty((nrhs, p.nt, p.m), dtype=torch.float64).pin_memory()
+        s.solve_host(fh, p0h, p1h, uh, rtol=rtol, maxit=maxit, stream=stream)  # staging warm-up
+        e2e_steps = max(1, min(args.steps, 20))
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            st, inf2 = s.solve_host(fh, p0h, p1h, uh, rtol=rtol, maxit=maxit, stream=stream)
+            if st != aao.AAO_OK:
+                raise RuntimeError(f"host solve failed {inf2}")
+        torch.cuda.synchronize(dev)
+        t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
+        barrier(world)
+        e2e = {"value": world * e2e_steps * nrhs / t_e2e, "unit": "solves/s",
+               "h2d_bytes_per_step": 8 * nrhs * (p.nt * p.m + 2 * p.m), "d2h_bytes_per_step": 8 * nrhs * p.nt * p.m,
+               "steps": e2e_steps, "api": "aao_solve_host"}
 
     out = None
     if rank == 0:

@@ -154,7 +154,8 @@ aao_status aao_apply_op(aao_handle* h, const double* x, double* y, int nrhs, voi
  * mode the time pipeline D^{-1} -> FFT -> x Sigma^{-1/2} -> iFFT -> D^2 ->
  * FFT -> x conj(Sigma^{-1/2}) -> iFFT -> D^{-1}, then the DSTs again.
  * r, z: nrhs x n x m device vectors; z may equal r (in place).  Uses the
- * handle's precision.  Errors: AAO_EINVAL, AAO_ECUDA. */
+ * handle's precision (in FP32 mode the first call allocates an FP32 staging vector
+ * of nrhs_max x n x m floats).  Errors: AAO_EINVAL, AAO_ECUDA, AAO_ENOMEM. */
 aao_status aao_apply_prec(aao_handle* h, const double* r, double* z, int nrhs, void* stream);
 
 /* y = (I_n (x) U) x with U = S (x) ... (x) S the orthonormal multi-dimensional
@@ -294,6 +295,17 @@ aao_status aao_serve_destroy(aao_server* s);
 
 /* Thread-local text of the last serving failure in this thread. */
 const char* aao_serve_last_error(void);
+
+/* Autotuner: pick, for this handle's shape and precision, the fastest variant of the
+ * time-pipeline kernel (FFT stage plan: radix-4 or radix-16 first; tile: 4096/n or
+ * 2048/n mode pairs per CTA; shared-memory layout: sequence-major or interleaved and
+ * padded) and of the DST kernel (radix-4 or radix-16 stage plan) by
+ * timing each on the handle's workspace with CUDA events (the work of the kernels is
+ * the same in every variant; only speed differs).  tune_file (host string, may be
+ * NULL): a text file of cached choices, one line "dim N nt precision time dst"; a
+ * matching line is applied without measuring, otherwise the measured choice is
+ * appended.  Synchronous.  Errors: AAO_EINVAL, AAO_ECUDA. */
+aao_status aao_autotune(aao_handle* h, const char* tune_file);
 
 /* Number of kernel launches this handle has issued since creation (statistics). */
 uint64_t aao_launch_count(const aao_handle* h);

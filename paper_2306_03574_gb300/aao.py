@@ -16,7 +16,7 @@ __all__ = [
     "AaoError", "AAO_OK", "AAO_EINVAL", "AAO_EUNSUPPORTED", "AAO_ENOMEM", "AAO_ECUDA",
     "AAO_ENOTCONV", "AAO_EBREAKDOWN", "AAO_ESINGULAR", "AAO_EBUSY", "AAO_EPENDING",
     "AAO_ETIMEOUT", "AAO_PREC_FP64", "AAO_PREC_FP32_IR", "lib", "lib_path", "header_functions",
-    "aao_create", "aao_destroy", "aao_set_coefficient", "aao_workspace_bytes", "aao_build_rhs", "aao_apply_op",
+    "aao_create", "aao_destroy", "aao_set_coefficient", "aao_autotune", "aao_workspace_bytes", "aao_build_rhs", "aao_apply_op",
     "aao_apply_prec", "aao_apply_dst", "aao_apply_time", "aao_minres_solve", "aao_solve_host",
     "aao_residual_norm", "aao_residual_norm_noalloc",
     "aao_launch_count", "aao_status_str", "aao_last_error", "aao_profile_enable", "aao_profile_read",
@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
             "aao_noalloc_last_error": ([], ctypes.c_char_p),
             "aao_status_str": ([i], ctypes.c_char_p),
             "aao_profile_enable": ([p, i], i),
+            "aao_autotune": ([p, ctypes.c_char_p], i),
             "aao_serve_create": ([ctypes.c_size_t, i, ctypes.POINTER(ctypes.c_void_p)], i),
             "aao_serve_submit": ([p, ctypes.POINTER(aao_request), ctypes.POINTER(ctypes.c_uint64)], i),
             "aao_serve_poll": ([p, ctypes.c_uint64, ctypes.POINTER(aao_serve_result)], i),
@@ -227,6 +228,10 @@ def aao_create(dim: int, N: int, nt: int, tau: float, alpha: float, c2: float = 
 
 def aao_set_coefficient(h, a_face, stream=None) -> None:
     _check(lib().aao_set_coefficient(h, _dev_ptr(a_face), _stream(stream)), "aao_set_coefficient")
+
+
+def aao_autotune(h, tune_file=None) -> None:
+    _check(lib().aao_autotune(h, tune_file.encode() if tune_file else None), "aao_autotune")
 
 
 def aao_destroy(h) -> None:
@@ -365,6 +370,9 @@ class Solver:
         self.nrhs_max = nrhs_max
         self.h = aao_create(dim, N, nt, tau, alpha, c2, precision, nrhs_max,
                             variable_coefficient=variable_coefficient, graph=graph)
+
+    def autotune(self, tune_file=None):
+        aao_autotune(self.h, tune_file)
 
     def set_coefficient(self, a_face, stream=None):
         aao_set_coefficient(self.h, a_face, stream)

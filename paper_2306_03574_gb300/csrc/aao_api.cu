@@ -81,13 +81,15 @@ struct aao_handle {
   bool use_graph = false;
   cudaStream_t cap_stream = nullptr;
   int* d_trips = nullptr;
-  int trips_host = 0;
+  int* trips_host = nullptr;  // pinned
   struct GraphCache {
     long key;
     double rtol;
     int maxit;
     cudaGraphExec_t exec;
+    uint64_t init_kernels, body_kernels;  // kernels in the initialisation / one loop trip
   };
+  uint64_t last_init_kernels = 0, last_body_kernels = 0;
   std::vector<GraphCache> graphs;
   float* f32 = nullptr;                          // FP32 preconditioner buffer
   double* partial = nullptr; int partial_stride = 0;  // 3 * nrhs_max * partial_stride
@@ -122,6 +124,7 @@ struct aao_handle {
     for (void* p : allocs) cudaFree(p);
     if (sc_host) cudaFreeHost(sc_host);
     if (relres_host) cudaFreeHost(relres_host);
+    if (trips_host) cudaFreeHost(trips_host);
   }
   template <typename T>
   aao_status alloc(T** p, size_t count) {
@@ -229,6 +232,7 @@ aao_status prec_apply(aao_handle* h, const double* in, double* out, int nrhs, cu
       AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
   } else {
     const size_t cnt = (size_t)nrhs * h->vlen();
+    if (!h->f32) AAO_TRY(h->alloc(&h->f32, (size_t)h->nrhs_max * h->vlen()));  // first FP32 apply_prec
     AAO_KL(h, KC_CAST, s, launch_cast(in, h->f32, cnt, s, &h->launches));
     for (int ax = 0; ax < P.d; ++ax)
       AAO_KL(h, KC_DST_X32 + ax, s, launch_dst_axis<float>(P, h->f32, h->f32, ax, nrhs, s, &h->launches));
@@ -396,6 +400,7 @@ aao_status minres_collect(aao_handle* h, int nrhs, aao_solve_info* info) {
 // Every pointer it touches belongs to the handle, so the graph is reused across solves.
 aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   aao_handle* h = c.h;
+  const uint64_t l0 = h->launches;  // launcher calls during capture are not launches
   MinresCtx cc = c;
   cudaStream_t cs = h->cap_stream;
   cc.s = cs;
@@ -421,8 +426,11 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamBeginCaptureToGraph");
   if (cudaMemsetAsync(h->d_trips, 0, sizeof(int), cs) != cudaSuccess ||
       minres_enqueue_init(cc, use_x0, B0) != AAO_OK ||
-      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 0, cs, nullptr) != cudaSuccess)
+      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 0, cs, &h->launches) != cudaSuccess) {
+    h->launches = l0;
     return fail_cleanup(cudaGetLastError(), "graph initialisation capture");
+  }
+  const uint64_t init_k = h->launches - l0;
   cudaStreamCaptureStatus cst;
   cudaGraph_t capg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -447,8 +455,13 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   if (e != cudaSuccess) return fail_cleanup(e, "capture of the loop body");
   const MinresBufs B1 = rotate(B0);
   if (minres_enqueue_iter(cc, B0) != AAO_OK || minres_enqueue_iter(cc, B1) != AAO_OK ||
-      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 1, cs, nullptr) != cudaSuccess)
+      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 1, cs, &h->launches) != cudaSuccess) {
+    h->launches = l0;
     return fail_cleanup(cudaGetLastError(), "loop body capture");
+  }
+  h->last_init_kernels = init_k;
+  h->last_body_kernels = h->launches - l0 - init_k;
+  h->launches = l0;
   cudaGraph_t bend = nullptr;
   e = cudaStreamEndCapture(cs, &bend);
   if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamEndCapture(body)");
@@ -485,9 +498,10 @@ aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_
     }
     AAO_CK(cudaGraphLaunch(ex, s));
     AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
-    AAO_CK(cudaMemcpyAsync(&h->trips_host, h->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AAO_CK(cudaMemcpyAsync(h->trips_host, h->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s));
     AAO_CK(cudaStreamSynchronize(s));
-    h->launches += 12 + (uint64_t)h->trips_host * 20;  // kernels the graph ran (approximate per trip)
+    // kernels the graph ran: the initialisation plus one body per loop trip
+    h->launches += h->last_init_kernels + (uint64_t)(*h->trips_host) * h->last_body_kernels;
     return minres_collect(h, nrhs, info);
   }
   AAO_TRY(minres_enqueue_init(c, use_x0, B0));
@@ -718,10 +732,13 @@ aao_status get_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   for (auto& gc : h->graphs)
     if (gc.key == key && gc.rtol == c.rtol && gc.maxit == c.maxit) {
       *out = gc.exec;
+      h->last_init_kernels = gc.init_kernels;
+      h->last_body_kernels = gc.body_kernels;
       return AAO_OK;
     }
   AAO_TRY(build_graph(c, use_x0, out));
-  h->graphs.push_back(aao_handle::GraphCache{key, c.rtol, c.maxit, *out});
+  h->graphs.push_back(aao_handle::GraphCache{key, c.rtol, c.maxit, *out, h->last_init_kernels,
+                                             h->last_body_kernels});
   return AAO_OK;
 }
 
@@ -750,6 +767,7 @@ aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double 
   AAO_TRY(get_graph(c, 0, &ex));
   AAO_CK(cudaGraphLaunch(ex, s));
   AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(MinresScalars), cudaMemcpyDeviceToHost, s));
+  AAO_CK(cudaMemcpyAsync(h->trips_host, h->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s));
   AAO_TRY(dst_apply(h, h->vxh, x, 1, s));
   double* p1 = h->partial;
   double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
@@ -762,6 +780,7 @@ aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double 
 }
 
 aao_status aaoi_solve_collect(aao_handle* h, double rtol, aao_solve_info* info) {
+  h->launches += h->last_init_kernels + (uint64_t)(*h->trips_host) * h->last_body_kernels;
   aao_status st = minres_collect(h, 1, info);
   info->relres_true = h->relres_host[0];
   if (info->relres_true > rtol && info->status == AAO_OK) info->status = AAO_ENOTCONV;
@@ -845,7 +864,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   P.coef = P.c2 * tau * tau / (2.0 * P.h * P.h);
   if (const char* tv = getenv("AAO_TIME_VARIANT")) {  // tuning override: "v64,v32"
     int a = 0, b = -1;
-    if (sscanf(tv, "%d,%d", &a, &b) >= 1) { P.time_variant64 = a & 3; P.time_variant32 = (b >= 0 ? b : a) & 3; }
+    if (sscanf(tv, "%d,%d", &a, &b) >= 1) { P.time_variant64 = a & 7; P.time_variant32 = (b >= 0 ? b : a) & 7; }
   }
   if (const char* dv = getenv("AAO_DST_VARIANT")) P.dst_variant = atoi(dv) & 1;
 
@@ -892,6 +911,12 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   if (o.graph) {
     h->use_graph = true;
     if ((st = h->alloc(&h->d_trips, 1))) return bail(st);
+    if (cudaMallocHost(&h->trips_host, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      h->trips_host = nullptr;
+      return bail(fail(AAO_ENOMEM, "cudaMallocHost failed"));
+    }
+    *h->trips_host = 0;
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       return bail(fail(AAO_ECUDA, "cudaStreamCreate failed"));
@@ -903,8 +928,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     if ((st = h->alloc(&h->face, fsz))) return bail(st);
   }
   if (fp32) {
-    if ((st = h->alloc(&h->vr, vl)) || (st = h->alloc(&h->vdx, vl)) || (st = h->alloc(&h->f32, vl)))
-      return bail(st);
+    if ((st = h->alloc(&h->vr, vl)) || (st = h->alloc(&h->vdx, vl))) return bail(st);
   }
   h->partial_stride = std::max(yt_blocks_per_rhs(P), dot_blocks_per_rhs(P));
   if ((st = h->alloc(&h->partial, (size_t)3 * h->nrhs_max * h->partial_stride)) ||
@@ -941,6 +965,86 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   st = run();
   if (st != AAO_OK) return bail(st);
   *out = h;
+  return AAO_OK;
+}
+
+aao_status aao_autotune(aao_handle* h, const char* tune_file) {
+  AAO_TRY(check_handle(h));
+  AAO_CK(cudaSetDevice(h->device));
+  Plan& P = h->P;
+  const int prec = h->precision;
+  if (tune_file) {  // cached choice?
+    if (FILE* fh = fopen(tune_file, "r")) {
+      int d, N, n, pr, tv, dv;
+      bool found = false;
+      while (fscanf(fh, "%d %d %d %d %d %d", &d, &N, &n, &pr, &tv, &dv) == 6)
+        if (d == P.d && N == P.N && n == P.n && pr == prec) {
+          if (prec == AAO_PREC_FP64) P.time_variant64 = tv & 7;
+          else P.time_variant32 = tv & 7;
+          P.dst_variant = dv & 1;
+          found = true;
+        }
+      fclose(fh);
+      if (found) {
+        AAO_CK(cudaDeviceSynchronize());
+        for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+        h->graphs.clear();
+        return AAO_OK;
+      }
+    }
+  }
+  cudaStream_t s = 0;
+  const size_t vb = h->vlen() * sizeof(double);
+  AAO_CK(cudaMemsetAsync(h->vv, 0, vb, s));
+  cudaEvent_t e0, e1;
+  AAO_CK(cudaEventCreate(&e0));
+  AAO_CK(cudaEventCreate(&e1));
+  auto timeit = [&](auto&& launch) -> float {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, s);
+      launch();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, ms);  // first run warms caches and attributes
+    }
+    return best;
+  };
+  int best_tv = 0;
+  float best_t = 1e30f;
+  for (int v = 0; v < 8; ++v) {
+    if (prec == AAO_PREC_FP64) P.time_variant64 = v;
+    else P.time_variant32 = v;
+    const float t = timeit([&]() {
+      if (prec == AAO_PREC_FP64) launch_time<double>(P, h->vv, h->vz, 1, s, nullptr);
+      else launch_time_mixed(P, h->vv, h->vz, 1, s, nullptr);
+    });
+    if (t < best_t) { best_t = t; best_tv = v; }
+  }
+  if (prec == AAO_PREC_FP64) P.time_variant64 = best_tv;
+  else P.time_variant32 = best_tv;
+  int best_dv = 0;
+  float best_d = 1e30f;
+  for (int v = 0; v < 2; ++v) {
+    P.dst_variant = v;
+    const float t = timeit([&]() { launch_dst_axis<double>(P, h->vv, h->vz, 0, 1, s, nullptr); });
+    if (t < best_d) { best_d = t; best_dv = v; }
+  }
+  P.dst_variant = best_dv;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  AAO_CK(cudaGetLastError());
+  AAO_CK(cudaDeviceSynchronize());
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old variants
+  h->graphs.clear();
+  if (tune_file) {
+    if (FILE* fh = fopen(tune_file, "a")) {
+      fprintf(fh, "%d %d %d %d %d %d\n", P.d, P.N, P.n, prec, best_tv, best_dv);
+      fclose(fh);
+    }
+  }
   return AAO_OK;
 }
 

@@ -5,12 +5,37 @@
 //
 // Each stage first loads every value it needs into registers, synchronises,
 // then writes the butterfly outputs back in place, so a single buffer serves
-// all stages.  Sequence q of the batch occupies buf[q*L .. q*L+L).
+// all stages.
+//
+// Two shared-memory layouts of the batch (template parameter LAY):
+//   0  sequence-major: element x of sequence q at q*L + x; the threads of a warp
+//      walk x.  Stockham writes of stride RX then fall on one bank (a 32-way
+//      conflict for radix 16), which costs little only where the FP64 pipe, not
+//      shared memory, is the bottleneck.
+//   1  interleaved and padded: element x of sequence q at NS*pad(x) + q with
+//      pad(x) = x + floor(x/16); the threads of a warp walk q first.  Reads,
+//      loads and stores touch consecutive words, the strided Stockham writes
+//      are spread over all banks by the one-in-16 padding, and the lanes of a
+//      warp share their twiddle factors (broadcast reads).
 #pragma once
 
 #include "aao_internal.cuh"
 
 namespace aao {
+
+template <int L, int NS, int LAY>
+struct SLay {
+  static constexpr int size = LAY ? NS * (L + L / 16) : NS * L;  // elements of the batch buffer
+  static __device__ __forceinline__ int at(int q, int x) {
+    return LAY ? NS * (x + (x >> 4)) + q : q * L + x;
+  }
+  // task -> (sequence q, index j) for a pass with Q tasks per sequence
+  template <int Q>
+  static __device__ __forceinline__ void split(int task, int& q, int& j) {
+    if (LAY) { q = task % NS; j = task / NS; }
+    else { q = task / Q; j = task % Q; }
+  }
+};
 
 template <int L>
 struct Log2 {
@@ -44,8 +69,9 @@ AAO_HD void dft4(C& v0, C& v1, C& v2, C& v3) {
 }
 
 // One radix-4 Stockham stage with span Ls (sub-transforms of length Ls done).
-template <int L, int NS, int NT, bool INV, typename C>
+template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
 __device__ __forceinline__ void fft_stage4(C* buf, const C* tw, int Ls) {
+  using Y = SLay<L, NS, LAY>;
   constexpr int Q = L / 4;
   constexpr int TASKS = NS * Q;
   static_assert(TASKS % NT == 0, "radix-4 tasks must divide evenly among threads");
@@ -53,17 +79,16 @@ __device__ __forceinline__ void fft_stage4(C* buf, const C* tw, int Ls) {
   C v[TPT][4];
 #pragma unroll
   for (int t = 0; t < TPT; ++t) {
-    const int task = threadIdx.x + t * NT;
-    const int q = task / Q, j = task % Q;
-    const C* p = buf + q * L + j;
+    int q, j;
+    Y::template split<Q>(threadIdx.x + t * NT, q, j);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) v[t][r] = p[r * Q];
+    for (int r = 0; r < 4; ++r) v[t][r] = buf[Y::at(q, j + r * Q)];
   }
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < TPT; ++t) {
-    const int task = threadIdx.x + t * NT;
-    const int q = task / Q, j = task % Q;
+    int q, j;
+    Y::template split<Q>(threadIdx.x + t * NT, q, j);
     const int k = j & (Ls - 1);
     if (Ls > 1) {
       const int step = (Q / Ls) * k;  // twiddle exponent r*k*L/(4 Ls)
@@ -72,16 +97,17 @@ __device__ __forceinline__ void fft_stage4(C* buf, const C* tw, int Ls) {
       v[t][3] = cmul(v[t][3], twid<INV>(tw[3 * step]));
     }
     dft4<INV>(v[t][0], v[t][1], v[t][2], v[t][3]);
-    C* o = buf + q * L + (j - k) * 4 + k;
+    const int o = (j - k) * 4 + k;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) o[r * Ls] = v[t][r];
+    for (int r = 0; r < 4; ++r) buf[Y::at(q, o + r * Ls)] = v[t][r];
   }
   __syncthreads();
 }
 
 // Final radix-2 stage (span L/2).
-template <int L, int NS, int NT, bool INV, typename C>
+template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
 __device__ __forceinline__ void fft_stage2_last(C* buf, const C* tw) {
+  using Y = SLay<L, NS, LAY>;
   constexpr int Q = L / 2;
   constexpr int TASKS = NS * Q;
   static_assert(TASKS % NT == 0, "radix-2 tasks must divide evenly among threads");
@@ -89,31 +115,31 @@ __device__ __forceinline__ void fft_stage2_last(C* buf, const C* tw) {
   C v[TPT][2];
 #pragma unroll
   for (int t = 0; t < TPT; ++t) {
-    const int task = threadIdx.x + t * NT;
-    const int q = task / Q, j = task % Q;
-    v[t][0] = buf[q * L + j];
-    v[t][1] = buf[q * L + j + Q];
+    int q, j;
+    Y::template split<Q>(threadIdx.x + t * NT, q, j);
+    v[t][0] = buf[Y::at(q, j)];
+    v[t][1] = buf[Y::at(q, j + Q)];
   }
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < TPT; ++t) {
-    const int task = threadIdx.x + t * NT;
-    const int q = task / Q, j = task % Q;
+    int q, j;
+    Y::template split<Q>(threadIdx.x + t * NT, q, j);
     const C b = cmul(v[t][1], twid<INV>(tw[j]));
-    buf[q * L + j] = cadd(v[t][0], b);
-    buf[q * L + j + Q] = csub(v[t][0], b);
+    buf[Y::at(q, j)] = cadd(v[t][0], b);
+    buf[Y::at(q, j + Q)] = csub(v[t][0], b);
   }
   __syncthreads();
 }
 
 // Full transform of NS sequences of length L by NT threads.  The caller must
 // have synchronised after writing buf; on return buf is synchronised too.
-template <int L, int NS, int NT, bool INV, typename C>
+template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
 __device__ __forceinline__ void fft_block(C* buf, const C* tw) {
   constexpr int LG = Log2<L>::value;
 #pragma unroll
-  for (int s = 0; s < LG / 2; ++s) fft_stage4<L, NS, NT, INV>(buf, tw, 1 << (2 * s));
-  if constexpr ((LG & 1) != 0) fft_stage2_last<L, NS, NT, INV>(buf, tw);
+  for (int s = 0; s < LG / 2; ++s) fft_stage4<L, NS, NT, INV, LAY>(buf, tw, 1 << (2 * s));
+  if constexpr ((LG & 1) != 0) fft_stage2_last<L, NS, NT, INV, LAY>(buf, tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -199,8 +225,9 @@ AAO_HD void dft_r(C* v) {
 // One radix-RX Stockham stage with span Ls (sub-transforms of length Ls done):
 // task j in [0, L/RX), k = j mod Ls, v_r = x[j + r L/RX], v_r *= w^{r k L/(RX Ls)},
 // DFT_RX, y[(j - k) RX + k + r Ls] = v_r.
-template <int L, int NS, int NT, int RX, bool INV, typename C>
+template <int L, int NS, int NT, int RX, bool INV, int LAY = 0, typename C>
 __device__ __forceinline__ void fft_stage_r(C* buf, const C* tw, int Ls) {
+  using Y = SLay<L, NS, LAY>;
   constexpr int Q = L / RX;
   constexpr int TASKS = NS * Q;
   static_assert(TASKS % NT == 0, "radix tasks must divide evenly among threads");
@@ -208,17 +235,16 @@ __device__ __forceinline__ void fft_stage_r(C* buf, const C* tw, int Ls) {
   C v[TPT][RX];
 #pragma unroll
   for (int t = 0; t < TPT; ++t) {
-    const int task = threadIdx.x + t * NT;
-    const int q = task / Q, j = task % Q;
-    const C* p = buf + q * L + j;
+    int q, j;
+    Y::template split<Q>(threadIdx.x + t * NT, q, j);
 #pragma unroll
-    for (int r = 0; r < RX; ++r) v[t][r] = p[r * Q];
+    for (int r = 0; r < RX; ++r) v[t][r] = buf[Y::at(q, j + r * Q)];
   }
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < TPT; ++t) {
-    const int task = threadIdx.x + t * NT;
-    const int q = task / Q, j = task % Q;
+    int q, j;
+    Y::template split<Q>(threadIdx.x + t * NT, q, j);
     const int k = j & (Ls - 1);
     if (Ls > 1) {
       const int step = (Q / Ls) * k;
@@ -226,34 +252,34 @@ __device__ __forceinline__ void fft_stage_r(C* buf, const C* tw, int Ls) {
       for (int r = 1; r < RX; ++r) v[t][r] = cmul(v[t][r], twid<INV>(tw[r * step]));
     }
     dft_r<RX, INV>(v[t]);
-    C* o = buf + q * L + (j - k) * RX + k;
+    const int o = (j - k) * RX + k;
 #pragma unroll
-    for (int r = 0; r < RX; ++r) o[r * Ls] = v[t][r];
+    for (int r = 0; r < RX; ++r) buf[Y::at(q, o + r * Ls)] = v[t][r];
   }
   __syncthreads();
 }
 
 // Stage plans with radix-16 first: 64 = 16*4, 128 = 16*8, 256 = 16*16,
 // 512 = 16*16*2, 1024 = 16*16*4.
-template <int L, int NS, int NT, bool INV, typename C>
+template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
 __device__ __forceinline__ void fft_block16(C* buf, const C* tw) {
   if constexpr (L == 64) {
-    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 4, INV>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 4, INV, LAY>(buf, tw, 16);
   } else if constexpr (L == 128) {
-    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 8, INV>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 8, INV, LAY>(buf, tw, 16);
   } else if constexpr (L == 256) {
-    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 16);
   } else if constexpr (L == 512) {
-    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 16);
-    fft_stage_r<L, NS, NT, 2, INV>(buf, tw, 256);
+    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 2, INV, LAY>(buf, tw, 256);
   } else {
-    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 16, INV>(buf, tw, 16);
-    fft_stage_r<L, NS, NT, 4, INV>(buf, tw, 256);
+    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
+    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 4, INV, LAY>(buf, tw, 256);
   }
 }
 

@@ -14,6 +14,13 @@
 // G_{n-k} = conj(G_k) gives A_{n-k} = conj(A_k), B_{n-k} = conj(B_k), so the
 // table holds k = 0..n/2 only.  A CTA owns 2*NS consecutive modes, all n time
 // levels of them staged in shared memory (coalesced rows of the time-major vector).
+//
+// Kernel variants (bits of the variant number): bit 0 = FFT stage plan (radix-4
+// or radix-16 first), bit 1 = tile (4096/n mode pairs x 256 threads or 2048/n x
+// 128), bit 2 = shared-memory layout of the batch (sequence-major or interleaved
+// and padded, see fft_smem.cuh).  All variants compute the same values; the
+// translation units k_time64.cu / k_time32.cu instantiate them per precision.
+#pragma once
 #include <type_traits>
 
 #include "aao_internal.cuh"
@@ -35,8 +42,9 @@ __device__ __forceinline__ C mix(C A, C B, C Z, C W) {
   return Y;
 }
 
-template <bool CONJ, int L, int NS, int NT, typename C>
+template <bool CONJ, int L, int NS, int NT, int LAY, typename C>
 __device__ __forceinline__ void mix_pass(C* cbuf, const C* __restrict__ ab, int npairs, int p0) {
+  using Y = SLay<L, NS, LAY>;
   constexpr int H = L / 2;
   for (int task = threadIdx.x; task < NS * (H + 1); task += NT) {
     const int q = task % NS, k = task / NS;
@@ -48,32 +56,34 @@ __device__ __forceinline__ void mix_pass(C* cbuf, const C* __restrict__ ab, int 
     } else {
       A.x = A.y = B.x = B.y = 0;
     }
-    C* s = cbuf + q * L;
+    const int ik = Y::at(q, k);
     if (k == 0 || k == H) {
-      const C Z = s[k];
-      s[k] = mix<CONJ>(A, B, Z, Z);
+      const C Z = cbuf[ik];
+      cbuf[ik] = mix<CONJ>(A, B, Z, Z);
     } else {
-      const C Zk = s[k], Zm = s[L - k];
-      s[k] = mix<CONJ>(A, B, Zk, Zm);
-      s[L - k] = mix<!CONJ>(A, B, Zm, Zk);
+      const int im = Y::at(q, L - k);
+      const C Zk = cbuf[ik], Zm = cbuf[im];
+      cbuf[ik] = mix<CONJ>(A, B, Zk, Zm);
+      cbuf[im] = mix<!CONJ>(A, B, Zm, Zk);
     }
   }
   __syncthreads();
 }
 
 // FFT stage plan: 0 = radix-4 stages (+ one radix-2), 1 = radix-16 first (fewer passes)
-template <int FFTV, int L, int NS, int NT, bool INV, typename C>
+template <int FFTV, int L, int NS, int NT, bool INV, int LAY, typename C>
 __device__ __forceinline__ void fft_run(C* buf, const C* tw) {
-  if constexpr (FFTV == 0) fft_block<L, NS, NT, INV>(buf, tw);
-  else fft_block16<L, NS, NT, INV>(buf, tw);
+  if constexpr (FFTV == 0) fft_block<L, NS, NT, INV, LAY>(buf, tw);
+  else fft_block16<L, NS, NT, INV, LAY>(buf, tw);
 }
 
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV>
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
+  using Y = SLay<L, NS, LAY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cbuf = reinterpret_cast<C*>(smem_raw);
-  C* tw = cbuf + NS * L;
+  C* tw = cbuf + Y::size;
   R* dinv = reinterpret_cast<R*>(tw + L);
   R* d2 = dinv + L;
 
@@ -97,32 +107,33 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
     C z;
     z.x = (sa < m) ? R(p[0]) * di : R(0);
     z.y = (sa + 1 < m) ? R(p[1]) * di : R(0);
-    cbuf[q * L + t] = z;
+    cbuf[Y::at(q, t)] = z;
   }
   __syncthreads();
 
   const int p0 = blockIdx.x * NS;
-  fft_run<FFTV, L, NS, NT, false>(cbuf, tw);
-  mix_pass<false, L, NS, NT>(cbuf, tb.ab, a.npairs, p0);
-  fft_run<FFTV, L, NS, NT, true>(cbuf, tw);
+  fft_run<FFTV, L, NS, NT, false, LAY>(cbuf, tw);
+  mix_pass<false, L, NS, NT, LAY>(cbuf, tb.ab, a.npairs, p0);
+  fft_run<FFTV, L, NS, NT, true, LAY>(cbuf, tw);
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
-    C z = cbuf[q * L + t];
+    const int i = Y::at(q, t);
+    C z = cbuf[i];
     z.x *= d2[t];
     z.y *= d2[t];
-    cbuf[q * L + t] = z;
+    cbuf[i] = z;
   }
   __syncthreads();
-  fft_run<FFTV, L, NS, NT, false>(cbuf, tw);
-  mix_pass<true, L, NS, NT>(cbuf, tb.ab, a.npairs, p0);
-  fft_run<FFTV, L, NS, NT, true>(cbuf, tw);
+  fft_run<FFTV, L, NS, NT, false, LAY>(cbuf, tw);
+  mix_pass<true, L, NS, NT, LAY>(cbuf, tb.ab, a.npairs, p0);
+  fft_run<FFTV, L, NS, NT, true, LAY>(cbuf, tw);
 
   // scale by D^{-1} and store
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
     const int sa = s0 + 2 * q;
     TIO* p = out + rb + (long long)t * m + sa;
-    const C z = cbuf[q * L + t];
+    const C z = cbuf[Y::at(q, t)];
     const R di = dinv[t];
     if (sa < m) p[0] = TIO(z.x * di);
     if (sa + 1 < m) p[1] = TIO(z.y * di);
@@ -130,15 +141,15 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
 }
 
 // Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV>
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY>
 static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
-  const size_t smem = sizeof(C) * (NS * L + L) + 2 * sizeof(R) * L;
+  const size_t smem = sizeof(C) * (SLay<L, NS, LAY>::size + L) + 2 * sizeof(R) * L;
   TimeArgs a;
   a.m = P.m;
   a.n = P.n;
   a.npairs = P.npairs;
-  auto kern = k_time<R, TIO, L, NS, NT, FFTV>;
+  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
   kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
@@ -148,11 +159,15 @@ static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int n
 template <typename R, typename TIO, int L>
 static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   const int v = std::is_same<R, double>::value ? P.time_variant64 : P.time_variant32;
-  switch (v & 3) {
-    case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0>(P, in, out, nrhs, s);
-    case 1: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1>(P, in, out, nrhs, s);
-    case 2: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 0>(P, in, out, nrhs, s);
-    default: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1>(P, in, out, nrhs, s);
+  switch (v & 7) {
+    case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0, 0>(P, in, out, nrhs, s);
+    case 1: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 0>(P, in, out, nrhs, s);
+    case 2: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 0, 0>(P, in, out, nrhs, s);
+    case 3: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 0>(P, in, out, nrhs, s);
+    case 4: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0, 1>(P, in, out, nrhs, s);
+    case 5: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1>(P, in, out, nrhs, s);
+    case 6: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 0, 1>(P, in, out, nrhs, s);
+    default: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1>(P, in, out, nrhs, s);
   }
 }
 
@@ -173,16 +188,5 @@ cudaError_t launch_time(const Plan& P, const R* in, R* out, int nrhs, cudaStream
   if (nl) ++*nl;
   return time_dispatch<R, R>(P, in, out, nrhs, s);
 }
-
-cudaError_t launch_time_mixed(const Plan& P, const double* in, double* out, int nrhs, cudaStream_t s,
-                              uint64_t* nl) {
-  if (nl) ++*nl;
-  return time_dispatch<float, double>(P, in, out, nrhs, s);
-}
-
-template cudaError_t launch_time<double>(const Plan&, const double*, double*, int, cudaStream_t,
-                                         uint64_t*);
-template cudaError_t launch_time<float>(const Plan&, const float*, float*, int, cudaStream_t,
-                                        uint64_t*);
 
 }  // namespace aao

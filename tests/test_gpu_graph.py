@@ -75,3 +75,24 @@ def test_graph_variable_coefficient_and_maxit():
     assert np.array_equal(got[0][2], got[1][2])
     assert got[0][3] == got[1][3] == aao.AAO_ENOTCONV
     assert got[0][4] == got[1][4] == 3
+
+
+def test_autotune_keeps_results_and_caches(tmp_path):
+    """The autotuner only changes speed: after tuning, P^{-1} and the solve still match
+    the oracle; the tune file is written and then read back."""
+    from oracle import fast as OF
+    d, N, nt, alpha = 2, 127, 128, 1e-2
+    tau = 1.0 / nt
+    x = W.random_field((nt, N * N), seed=1500)
+    ref = OF.ABACPreconditioner(d, N, nt, tau, alpha).apply(x)
+    tf = str(tmp_path / "tune.txt")
+    for _ in range(2):  # measure + write, then read back
+        with aao.Solver(d, N, nt, tau, alpha, graph=True) as s:
+            s.autotune(tf)
+            xt = cu(x)
+            zt = torch.empty_like(xt)
+            s.apply_prec(xt, zt)
+            torch.cuda.synchronize()
+            assert np.abs(zt.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-12
+    lines = open(tf).read().strip().splitlines()
+    assert len(lines) == 1 and lines[0].split()[:4] == ["2", "127", "128", "0"]

@@ -74,30 +74,41 @@ def test_mixed_requests_equal_solo_solves():
         assert res["t_submit"] <= res["t_start"] <= res["t_done"]
 
 
+def _submit_wait(srv, p, tol=1e-8):
+    f, p0, p1 = cu(p.f), cu(p.psi0), cu(p.psi1)
+    x = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
+    t = aao.aao_serve_submit(srv, p.d, p.N, p.nt, p.tau, p.alpha, p.c2, tol, 100, f, p0, p1, x)
+    return aao.aao_serve_wait(srv, t, 120.0)
+
+
 def test_budget_eviction_and_oversize():
-    reqs = _requests(k=10, seed=78)
-    one = max(10 * p.nt * p.m * 8 for (_, p, *_rest) in reqs)
-    srv = aao.aao_serve_create(int(2.5 * one), 2)
+    """Two shapes of nearly equal footprint under a budget that holds only one: every
+    switch of shape evicts the idle handle of the other; a request larger than the
+    budget completes with AAO_ENOMEM."""
+    pa = W.config_2d(N=127, nt=128, alpha=1e-6)
+    pb = W.config_2d(N=63, nt=512, alpha=1e-6)
+    sizes = []
+    for p in (pa, pb):  # the pool bytes one handle of each shape takes
+        srv = aao.aao_serve_create(8 << 30, 1)
+        try:
+            assert _submit_wait(srv, p)[0] == aao.AAO_OK
+            sizes.append(aao.aao_serve_stats(srv)["pool_bytes"])
+        finally:
+            aao.aao_serve_destroy(srv)
+    budget = int(1.5 * max(sizes))
+    srv = aao.aao_serve_create(budget, 2)
     try:
-        tickets = [aao.aao_serve_submit(srv, p.d, p.N, p.nt, p.tau, p.alpha, p.c2, r["tol"], 100, f, p0, p1, x)
-                   for (r, p, f, p0, p1, x) in reqs]
-        for t in tickets:
-            st, res = aao.aao_serve_wait(srv, t, 120.0)
-            assert st == aao.AAO_OK
+        for p in (pa, pb, pa, pb):
+            assert _submit_wait(srv, p)[0] == aao.AAO_OK
         stats = aao.aao_serve_stats(srv)
-        assert stats["peak_pool_bytes"] <= stats["budget"]
+        assert stats["peak_pool_bytes"] <= budget
+        assert stats["evictions"] >= 3 and stats["handles_created"] == 4
         # a request that can never fit completes with AAO_ENOMEM
-        p = W.config_2d(N=255, nt=512, alpha=1e-6)
-        f, p0, p1 = cu(p.f), cu(p.psi0), cu(p.psi1)
-        x = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
-        t = aao.aao_serve_submit(srv, 2, 255, 512, p.tau, 1e-6, 1.0, 1e-8, 50, f, p0, p1, x)
-        st, res = aao.aao_serve_wait(srv, t, 60.0)
-        assert st == aao.AAO_ENOMEM
+        assert _submit_wait(srv, W.config_2d(N=255, nt=512, alpha=1e-6))[0] == aao.AAO_ENOMEM
         # unknown ticket
         assert aao.aao_serve_poll(srv, 123456789)[0] == aao.AAO_EINVAL
     finally:
         aao.aao_serve_destroy(srv)
-    assert stats["evictions"] >= 1
 
 
 def test_bounded_wait_times_out_then_completes():

@@ -1,0 +1,103 @@
+"""Every kernel variant computes the same values: the eight time-pipeline variants
+(FFT stage plan x tile x shared-memory layout) and the two DST stage plans, each
+against the oracle in FP64 and in FP32, at every supported time length with ragged
+mode tails.  The variants only change speed, so each must pass the same gates."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fast as OF
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2306_03574_gb300 as aao  # noqa: E402
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2306_03574_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    aao.lib()
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def relerr(a, b):
+    e = float(np.abs(a - b).max() / np.abs(b).max())
+    log = os.environ.get("AAO_PARITY_LOG")
+    if log:
+        with open(log, "a") as fh:
+            fh.write(f"{os.environ.get('PYTEST_CURRENT_TEST', '?').split(' ')[0]}\t{e:.3e}\n")
+    return e
+
+
+# (d, N, nt): every time length, mode counts that leave a partial last tile
+CASES = [(2, 63, 64), (2, 63, 128), (1, 255, 256), (2, 63, 256), (1, 511, 512), (1, 255, 1024)]
+ALPHA = 1e-2
+
+
+def _time_ref(d, N, nt, x):
+    pc = OF.ABACPreconditioner(d, N, nt, 1.0 / nt, ALPHA)
+    S = OF.dst_matrix(N)
+    return OF.apply_space(pc.apply(OF.apply_space(x, S, d, N)), S, d, N)
+
+
+@pytest.mark.parametrize("d,N,nt", CASES)
+def test_time_variants(d, N, nt, monkeypatch):
+    x = W.random_field((nt, N ** d), seed=1700 + nt + N)
+    ref = _time_ref(d, N, nt, x)
+    tol32 = 64 * EPS32 * np.log2(nt) * ALPHA ** (-(nt - 1) / nt)
+    outs = []
+    for v in range(8):
+        monkeypatch.setenv("AAO_TIME_VARIANT", f"{v},{v}")
+        for prec in (aao.AAO_PREC_FP64, aao.AAO_PREC_FP32_IR):
+            with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=prec) as s:
+                xt = cu(x)
+                yt = torch.empty_like(xt)
+                s.apply_time(xt, yt)
+                torch.cuda.synchronize()
+                y = yt.cpu().numpy()
+            if prec == aao.AAO_PREC_FP64:
+                assert relerr(y, ref) < 1e-12, (v, "fp64")
+                outs.append(y)
+            else:
+                assert relerr(y, ref) < tol32, (v, "fp32")
+    # the FP64 variants differ only in rounding order
+    for y in outs[1:]:
+        assert np.abs(y - outs[0]).max() <= 1e-13 * np.abs(outs[0]).max()
+
+
+@pytest.mark.parametrize("d,N,nt", [(2, 63, 64), (2, 127, 64), (2, 255, 64), (2, 511, 64), (3, 63, 64)])
+def test_dst_and_prec_variants(d, N, nt, monkeypatch):
+    """Both DST stage plans, along every axis, in FP64 (apply_dst) and FP32 (the
+    FP32 P_alpha^{-1}, which runs the FP32 DST and the FP32-vector time kernel)."""
+    m = N ** d
+    x = W.random_field((nt, m), seed=1800 + N + d)
+    S = OF.dst_matrix(N)
+    ref_dst = OF.apply_space(x, S, d, N)
+    ref_prec = OF.ABACPreconditioner(d, N, nt, 1.0 / nt, ALPHA).apply(x)
+    tol32 = 64 * EPS32 * np.log2(nt) * ALPHA ** (-(nt - 1) / nt)
+    for dv in range(2):
+        for tv in (1, 5):
+            monkeypatch.setenv("AAO_DST_VARIANT", str(dv))
+            monkeypatch.setenv("AAO_TIME_VARIANT", f"{tv},{tv}")
+            with aao.Solver(d, N, nt, 1.0 / nt, ALPHA) as s:
+                xt = cu(x)
+                yt = torch.empty_like(xt)
+                s.apply_dst(xt, yt)
+                torch.cuda.synchronize()
+                assert relerr(yt.cpu().numpy(), ref_dst) < 1e-13, (dv, tv)
+            with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=aao.AAO_PREC_FP32_IR) as s:
+                xt = cu(x)
+                zt = torch.empty_like(xt)
+                s.apply_prec(xt, zt)
+                torch.cuda.synchronize()
+                assert relerr(zt.cpu().numpy(), ref_prec) < tol32, (dv, tv)
