@@ -167,8 +167,9 @@ aao_status aao_apply_dst(aao_handle* h, const double* x, double* y, int nrhs, vo
 /* The time part of P_alpha^{-1} on DST coefficients: for every spatial mode j
  * the n x n map D^{-1} F^* G_j F D^2 F G_j F^* D^{-1} (G_j = diag of
  * Sigma_{k,j}^{-1/2}; Section 2.3 with U factored out), so that
- * apply_prec = apply_dst o apply_time o apply_dst.  x, y may be equal.  FP64.
- * Errors: AAO_EINVAL, AAO_ECUDA. */
+ * apply_prec = apply_dst o apply_time o apply_dst.  x, y may be equal.  FP64
+ * vectors; the arithmetic is the handle's precision (FP32/complex64 for
+ * AAO_PREC_FP32_IR, converted on load and store).  Errors: AAO_EINVAL, AAO_ECUDA. */
 aao_status aao_apply_time(aao_handle* h, const double* x, double* y, int nrhs, void* stream);
 
 /* Preconditioned MINRES on Y T x = b with P_alpha (eq. (precsys); Section 3:
@@ -304,8 +305,10 @@ const char* aao_serve_last_error(void);
  * the same in every variant; only speed differs).  tune_file (host string, may be
  * NULL): a text file of cached choices, one line "dim N nt precision time dst"; a
  * matching line is applied without measuring, otherwise the measured choice is
- * appended.  Synchronous.  Errors: AAO_EINVAL, AAO_ECUDA. */
-aao_status aao_autotune(aao_handle* h, const char* tune_file);
+ * appended.  chosen (host, may be NULL): receives {time variant, DST variant}.
+ * Synchronous; must not overlap other calls on the handle.  Errors: AAO_EINVAL,
+ * AAO_ECUDA. */
+aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen);
 
 /* Number of kernel launches this handle has issued since creation (statistics). */
 uint64_t aao_launch_count(const aao_handle* h);

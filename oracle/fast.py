@@ -202,3 +202,25 @@ def apply_C_alpha_direct(v: np.ndarray, d: int, N: int, tau: float, alpha: float
     out[0] += alpha * Lv_prev - 2.0 * alpha * v[n - 1]
     out[1] += alpha * Lv_last
     return out
+
+
+def time_part_modes(d: int, N: int, n: int, tau: float, alpha: float, Yh: np.ndarray, modes,
+                    c2: float = 1.0) -> np.ndarray:
+    """(I_n (x) U) P_alpha^{-1} (I_n (x) U) restricted to chosen spatial modes.
+
+    Yh (n, len(modes)) holds the DST-basis time series of the modes listed in `modes`
+    (column indices of U).  Writing P_alpha^{-1} = C^{-1/2} (C^{-1/2})^T with the
+    factors of Section 2.3 and using U U = I between them, the DST-basis map acts on
+    the time series of mode j alone:
+        z_j = (D^{-1} F^*) G_j (F D)(F D)^T G_j (D^{-1} F^*)^T y_j,
+    G_j = diag_k Sigma_{k,j}^{-1/2} (the time factors of Steps 1-3, twice).  Only the
+    Sigma columns of the chosen modes are formed, so any grid size can be sampled."""
+    Lam_m1 = L_eigenvalues_minus_one(d, N, tau, c2)[np.asarray(modes)]
+    g = 1.0 / np.sqrt(Sigma(n, alpha, Lam_m1))       # (n, len(modes)), principal branch
+    F = fourier_matrix(n)
+    dg = D_alpha_diag(n, alpha)
+    FD = F * dg[None, :]
+    DinvFs = (1.0 / dg)[:, None] * F.conj().T
+    a = g * (DinvFs.T @ Yh.astype(np.complex128))   # (C^{-1/2})^T: Steps 1 and 2
+    c = g * (FD @ (FD.T @ a))                        # its Step 3, then C^{-1/2}'s right factor and diagonal
+    return (DinvFs @ c).real.copy()                  # C^{-1/2}'s left factor

@@ -116,7 +116,7 @@ def lib() -> ctypes.CDLL:
             "aao_noalloc_last_error": ([], ctypes.c_char_p),
             "aao_status_str": ([i], ctypes.c_char_p),
             "aao_profile_enable": ([p, i], i),
-            "aao_autotune": ([p, ctypes.c_char_p], i),
+            "aao_autotune": ([p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)], i),
             "aao_serve_create": ([ctypes.c_size_t, i, ctypes.POINTER(ctypes.c_void_p)], i),
             "aao_serve_submit": ([p, ctypes.POINTER(aao_request), ctypes.POINTER(ctypes.c_uint64)], i),
             "aao_serve_poll": ([p, ctypes.c_uint64, ctypes.POINTER(aao_serve_result)], i),
@@ -230,8 +230,10 @@ def aao_set_coefficient(h, a_face, stream=None) -> None:
     _check(lib().aao_set_coefficient(h, _dev_ptr(a_face), _stream(stream)), "aao_set_coefficient")
 
 
-def aao_autotune(h, tune_file=None) -> None:
-    _check(lib().aao_autotune(h, tune_file.encode() if tune_file else None), "aao_autotune")
+def aao_autotune(h, tune_file=None) -> dict:
+    ch = (ctypes.c_int * 2)()
+    _check(lib().aao_autotune(h, tune_file.encode() if tune_file else None, ch), "aao_autotune")
+    return {"time_variant": ch[0], "dst_variant": ch[1]}
 
 
 def aao_destroy(h) -> None:
@@ -371,8 +373,8 @@ class Solver:
         self.h = aao_create(dim, N, nt, tau, alpha, c2, precision, nrhs_max,
                             variable_coefficient=variable_coefficient, graph=graph)
 
-    def autotune(self, tune_file=None):
-        aao_autotune(self.h, tune_file)
+    def autotune(self, tune_file=None) -> dict:
+        return aao_autotune(self.h, tune_file)
 
     def set_coefficient(self, a_face, stream=None):
         aao_set_coefficient(self.h, a_face, stream)

@@ -968,7 +968,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   return AAO_OK;
 }
 
-aao_status aao_autotune(aao_handle* h, const char* tune_file) {
+aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   AAO_TRY(check_handle(h));
   AAO_CK(cudaSetDevice(h->device));
   Plan& P = h->P;
@@ -986,6 +986,10 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file) {
         }
       fclose(fh);
       if (found) {
+        if (chosen) {
+          chosen[0] = prec == AAO_PREC_FP64 ? P.time_variant64 : P.time_variant32;
+          chosen[1] = P.dst_variant;
+        }
         AAO_CK(cudaDeviceSynchronize());
         for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
         h->graphs.clear();
@@ -1033,6 +1037,10 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file) {
     if (t < best_d) { best_d = t; best_dv = v; }
   }
   P.dst_variant = best_dv;
+  if (chosen) {
+    chosen[0] = best_tv;
+    chosen[1] = best_dv;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   AAO_CK(cudaGetLastError());
@@ -1143,8 +1151,7 @@ aao_status aao_apply_dst(aao_handle* h, const double* x, double* y, int nrhs, vo
 aao_status aao_apply_time(aao_handle* h, const double* x, double* y, int nrhs, void* stream) {
   AAO_TRY(check_call(h, nrhs));
   if (!x || !y) return fail(AAO_EINVAL, "null pointer");
-  AAO_KL(h, KC_TIME64, (cudaStream_t)stream, launch_time<double>(h->P, x, y, nrhs, (cudaStream_t)stream, &h->launches));
-  return AAO_OK;
+  return time_apply(h, x, y, nrhs, (cudaStream_t)stream);
 }
 
 aao_status aao_minres_solve(aao_handle* h, const double* b, double* x, int use_x0, int nrhs,

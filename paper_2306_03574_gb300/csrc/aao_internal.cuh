@@ -59,9 +59,11 @@ struct Plan {
   int d = 0, N = 0, M = 0, n = 0, m = 0, npairs = 0;
   double tau = 0, alpha = 0, c2 = 0, h = 0;
   double coef = 0;  // c2 tau^2 / (2 h^2): L w = w - coef * (sum of neighbour differences)
-  // time-kernel variant per precision: bit 0 = radix-16 stage plan, bit 1 = half-size tile
-  // (radix-16 + half tile measured fastest on GB300 for both precisions)
-  int time_variant64 = 3, time_variant32 = 3;
+  // time-kernel variant per precision: bit 0 = radix-16 stage plan, bit 1 = half-size
+  // tile, bit 2 = interleaved padded shared-memory layout.  Defaults measured on GB300:
+  // FP64 (FP64-pipe bound) radix-16 + half tile, layout immaterial (within 1 %);
+  // FP32 radix-16 + full tile + interleaved layout (bank conflicts dominate otherwise).
+  int time_variant64 = 7, time_variant32 = 5;
   // DST stage plan: 0 = radix-4, 1 = radix-16 first
   int dst_variant = 1;
   PrecTables<double> t64;

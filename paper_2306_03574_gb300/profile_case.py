@@ -6,6 +6,7 @@ applications (or full solves) of one problem size through the C ABI.
 from __future__ import annotations
 
 import argparse
+import os
 
 import numpy as np
 import torch
@@ -21,9 +22,15 @@ def main():
     ap.add_argument("--alpha", type=float, default=1e-6)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
-    ap.add_argument("--what", choices=["prec", "op", "solve"], default="prec")
+    ap.add_argument("--what", choices=["prec", "time", "dst", "op", "solve"], default="prec")
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--time-variant", type=int, default=None, help="time-kernel variant 0..7")
+    ap.add_argument("--dst-variant", type=int, default=None, help="DST variant 0..1")
     a = ap.parse_args()
+    if a.time_variant is not None:
+        os.environ["AAO_TIME_VARIANT"] = f"{a.time_variant},{a.time_variant}"
+    if a.dst_variant is not None:
+        os.environ["AAO_DST_VARIANT"] = str(a.dst_variant)
     prec = aao.AAO_PREC_FP64 if a.precision == "fp64" else aao.AAO_PREC_FP32_IR
     m = a.N ** a.d
     rng = np.random.default_rng(1)
@@ -33,6 +40,10 @@ def main():
         for _ in range(a.reps):
             if a.what == "prec":
                 s.apply_prec(x, y)
+            elif a.what == "time":
+                s.apply_time(x, y)
+            elif a.what == "dst":
+                s.apply_dst(x, y)
             elif a.what == "op":
                 s.apply_op(x, y)
             else:

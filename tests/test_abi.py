@@ -63,6 +63,8 @@ def test_null_pointers_rejected(L):
     assert L.aao_launch_count(None) == 0
     assert L.aao_apply_prec(None, None, None, 1, None) == aao.AAO_EINVAL
     assert L.aao_minres_solve(None, None, None, 0, 1, 1e-8, 10, None, None) == aao.AAO_EINVAL
+    assert L.aao_autotune(None, None, None) == aao.AAO_EINVAL
+    assert L.aao_set_coefficient(None, None, None) == aao.AAO_EINVAL
 
 
 def test_serve_argument_validation(L):

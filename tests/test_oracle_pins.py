@@ -443,3 +443,21 @@ def test_error_metric_closed_form():
     u = ex + 0.5
     h = 1.0 / (N + 1)
     assert abs(S.error_E(u, ex, d, h) - h * 0.5 * N) < 1e-15
+
+
+@pytest.mark.parametrize("d,N,n,alpha,c2", [(1, 15, 16, 1e-2, 1.0), (2, 7, 8, 1e-3, 1.7), (3, 3, 8, 0.3, 0.5)])
+def test_time_part_modes_equals_full_preconditioner(d, N, n, alpha, c2):
+    """The sampled DST-basis time map equals (I (x) U) P^{-1} (I (x) U) computed with the
+    full three-step procedure (explicit DSTs), on every mode and on a subset."""
+    tau = 1.0 / n
+    m = N ** d
+    rng = np.random.default_rng(5)
+    Yh = rng.standard_normal((n, m))
+    pc = F.ABACPreconditioner(d, N, n, tau, alpha, c2=c2)
+    S = F.dst_matrix(N)
+    full = F.apply_space(pc.apply(F.apply_space(Yh, S, d, N)), S, d, N)
+    allm = F.time_part_modes(d, N, n, tau, alpha, Yh, np.arange(m), c2=c2)
+    assert np.abs(allm - full).max() <= 1e-12 * np.abs(full).max()
+    sub = np.array([0, m // 3, m - 1])
+    part = F.time_part_modes(d, N, n, tau, alpha, Yh[:, sub], sub, c2=c2)
+    assert np.abs(part - full[:, sub]).max() <= 1e-12 * np.abs(full).max()
