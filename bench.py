@@ -57,6 +57,7 @@ WORKLOADS = {
                                 precision="fp32", varcoef=True),
 }
 WORKLOAD = dict(WORKLOADS["2d255_fp64"])
+WORKLOAD_NAME = ["2d255_fp64"]
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -114,7 +115,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int = 0, period_ms: int = 100):
+    def __init__(self, index: int = 0, period_ms: int = 50):
         self.proc = None
         self.path = None
         self.index = index
@@ -170,9 +171,10 @@ def source_hash(paths):
     return h.hexdigest()[:16]
 
 
-def traffic_record(cls: str):
-    """ncu DRAM bytes per launch for the dominant kernel, if captured for the
-    current kernel source (profiles/traffic.json, written from an ncu capture)."""
+def traffic_record(cls: str, variant=None):
+    """ncu DRAM bytes per launch for the dominant kernel, if captured for the current
+    kernel source and the kernel variant the bench runs (profiles/traffic.json,
+    written from an ncu capture)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -187,6 +189,10 @@ def traffic_record(cls: str):
         if source_hash(srcs) != r.get("source_hash"):
             return None
     except Exception:
+        return None
+    if variant is not None and r.get("variant") is not None and r["variant"] != variant:
+        return None
+    if r.get("workload") != WORKLOAD_NAME[0]:
         return None
     return r.get("bytes_per_launch")
 
@@ -301,6 +307,81 @@ def workload_config(unknowns, name=None):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def error_vs_exact(x_host, p):
+    """E = max_k h^{d/2} ||u^(k) - u(x, k tau)||_2 over the time levels (the error
+    measure of the paper's Section 3), for problems with a known exact solution."""
+    import numpy as np
+    if p.exact is None:
+        return None
+    h = 1.0 / (p.N + 1)
+    worst = 0.0
+    for k in range(p.nt):
+        diff = x_host[k] - p.exact((k + 1) * p.tau)
+        worst = max(worst, float(h ** (p.d / 2.0) * np.linalg.norm(diff)))
+    return worst
+
+
+def cufft_comparison(s, p, dev, reps=10):
+    """The time part of P_alpha^{-1} written with torch.fft (cuFFT) and torch elementwise
+    kernels: D^{-1}, rfft, x G, irfft, D^2, rfft, x conj(G), irfft, D^{-1} along time for
+    every DST mode, G = Sigma^{-1/2} on bins k = 0..n/2.  A library baseline for the
+    fused kernel (timed the same way on the same data), not part of the product."""
+    import math
+    import torch
+    d, N, n, tau, alpha, c2 = p.d, p.N, p.nt, p.tau, p.alpha, p.c2
+    m = N ** d
+    f64, c128 = torch.float64, torch.complex128
+    h = 1.0 / (N + 1)
+    j = torch.arange(1, N + 1, dtype=f64, device=dev)
+    mu1 = 4.0 / (h * h) * torch.sin(j * math.pi * h / 2.0) ** 2
+    mu = torch.zeros((N,) * d, dtype=f64, device=dev)
+    for a in range(d):
+        shp = [1] * d
+        shp[d - 1 - a] = N
+        mu = mu + mu1.reshape(shp)
+    lm1 = (0.5 * c2 * tau * tau * mu).reshape(1, m)
+    k = torch.arange(n // 2 + 1, dtype=f64, device=dev).reshape(-1, 1)
+    la = math.log(alpha) / n
+    a = math.exp(la)
+    th = torch.exp(1j * (2 * math.pi / n) * k.to(c128))
+    sig = (1 - a * th) ** 2 + lm1.to(c128) * (1 + a * a * th * th)
+    G = sig ** -0.5
+    t = torch.arange(n, dtype=f64, device=dev).reshape(-1, 1)
+    dinv = alpha ** (-t / n)
+    d2 = alpha ** (2 * t / n)
+    x = torch.randn((n, m), dtype=f64, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+
+    def pipe(v):
+        z = torch.fft.irfft(G * torch.fft.rfft(v * dinv, dim=0), n=n, dim=0)
+        z = torch.fft.irfft(G.conj() * torch.fft.rfft(z * d2, dim=0), n=n, dim=0)
+        return z * dinv
+
+    ours = torch.empty_like(x)
+    for _ in range(3):
+        ref = pipe(x)
+        s.apply_time(x, ours)
+    torch.cuda.synchronize(dev)
+    diff = float((ref - ours).abs().max() / ref.abs().max())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        pipe(x)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_lib = e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps):
+        s.apply_time(x, ours)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_ours = e0.elapsed_time(e1) / reps
+    return {"time_pipeline_ms_cufft": t_lib, "time_pipeline_ms_fused_kernel": t_ours,
+            "speedup": t_lib / t_ours, "max_rel_diff": diff,
+            "note": "torch.fft (cuFFT) rfft/irfft along time + torch elementwise kernels, FP64, "
+                    "same shape; CUDA events, mean of %d" % reps}
+
+
 
 def run_gpu(args, world, rank, local):
     import numpy as np
@@ -424,7 +505,11 @@ def run_gpu(args, world, rank, local):
                 "peak_note": "measured copy bandwidth (of measured)"}
 
     roofline = roof(dom)
-    roofline["traffic"] = traffic_record(dom)
+    var = None
+    if variants:
+        var = variants["time_variant"] if dom.startswith("time") else (
+            variants["dst_variant"] if dom.startswith("dst") else None)
+    roofline["traffic"] = traffic_record(dom, var)
     for k in kern:
         if algorithmic_flops(k, d, p.N, p.nt, unknowns):
             r = roof(k)
@@ -462,6 +547,23 @@ def run_gpu(args, world, rank, local):
                "h2d_bytes_per_step": 8 * nrhs * (p.nt * p.m + 2 * p.m), "d2h_bytes_per_step": 8 * nrhs * p.nt * p.m,
                "steps": e2e_steps, "api": "aao_solve_host"}
 
+    # ---- accuracy against the exact solution, the FP64 path and a cuFFT pipeline ----
+    extra = {}
+    if not varcoef and d < 3:
+        xh = x[0].cpu().numpy()
+        extra["error_vs_exact"] = error_vs_exact(xh, p)
+        if WORKLOAD["precision"] != "fp64":
+            with aao.Solver(d, p.N, p.nt, p.tau, p.alpha, nrhs_max=1, graph=args.graph) as s64:
+                x64 = torch.empty_like(x[0])
+                st64, info64 = s64.solve(b[0], x64, rtol=rtol, maxit=maxit, stream=stream)
+                torch.cuda.synchronize(dev)
+                extra["vs_fp64_gpu"] = {
+                    "rel_diff_2norm": float(torch.linalg.norm(x[0] - x64) / torch.linalg.norm(x64)),
+                    "fp64_iters": info64[0]["iters"], "fp64_relres_true": info64[0]["relres_true"],
+                    "fp64_error_vs_exact": error_vs_exact(x64.cpu().numpy(), p)}
+        elif d == 2 and rank == 0:
+            extra["cufft_comparison"] = cufft_comparison(s, p, dev)
+
     out = None
     if rank == 0:
         cpu = None
@@ -484,13 +586,14 @@ def run_gpu(args, world, rank, local):
             "prec_apply": prec, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "kernels": kern, "kernel_variants": variants,
         }
+        out.update(extra)
         print(json.dumps(out), flush=True)
     s.close()
     return 0
 
 
 def run_served(args, world, rank, local):
-    """Served stream: Poisson arrivals (mean 200/s, seeded) of 1D/2D requests with mixed
+    """Served stream: Poisson arrivals (mean --rate/s, default 200, seeded) of 1D/2D requests with mixed
     sizes, wave speeds and tolerances, admitted under a 120 GB HBM budget; replayed in
     real time; latency = completion - submission on the server's clock."""
     import numpy as np
@@ -502,7 +605,8 @@ def run_served(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     count = args.requests
-    reqs = W.served_requests(count=count, rate=200.0, seed=5 + rank)
+    rate = float(args.rate)
+    reqs = W.served_requests(count=count, rate=rate, seed=5 + rank)
     # per-shape device data (source, initial values) shared by the requests of that shape;
     # wave speed, tolerance and the output buffer differ per request
     shapes = {}
@@ -581,15 +685,15 @@ def run_served(args, world, rank, local):
             same &= bool(np.array_equal(x1.cpu().numpy(), xs))
     unknowns = sum(rr["nt"] * rr["N"] ** rr["d"] for rr, _ in ok)
     line = {
-        "metric": "served solves/s with p50/p99 latency (Poisson 200/s, mixed 1D/2D, 120 GB budget)",
+        "metric": f"served solves/s with p50/p99 latency (Poisson {rate:g}/s, mixed 1D/2D, 120 GB budget)",
         "value": len(ok) / (t_last - t_first), "unit": "solves/s", "n_gpus": world,
         "steps": len(reqs), "warmup": len(shapes), "ms_per_step": 1e3 * (t_last - t_first) / max(len(ok), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "served_poisson200_mixed_1d2d_fp64", "requests": len(reqs), "slots": args.slots,
+        "config": {"workload": f"served_poisson{rate:g}_mixed_1d2d_fp64", "requests": len(reqs), "slots": args.slots,
                    "budget_bytes": int(120e9), "shapes": len(shapes)},
         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                        "mean": float(lat.mean() * 1e3), "max": float(lat.max() * 1e3)},
-        "completed": len(ok), "failed": len(done) - len(ok), "offered_rate": 200.0,
+        "completed": len(ok), "failed": len(done) - len(ok), "offered_rate": rate,
         "unknowns_per_s": unknowns / (t_last - t_first), "iters_mean": float(np.mean([res["iters"] for _, res in ok])),
         "server": stats, "sample_equal_alone": same, "sample_size": len(sample),
     }
@@ -601,13 +705,14 @@ def run_served(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served"], default="2d255_fp64")
     ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="served workload: concurrent solves")
+    ap.add_argument("--rate", type=float, default=200.0, help="served workload: mean Poisson arrival rate (1/s)")
     ap.add_argument("--alpha", type=float, default=None)
     ap.add_argument("--graph", type=int, default=1,
                     help="1: solve loop captured in a CUDA graph (device-side while loop); 0: host-driven")
@@ -617,6 +722,7 @@ def main():
     if args.workload != "served":
         WORKLOAD.clear()
         WORKLOAD.update(WORKLOADS[args.workload])
+        WORKLOAD_NAME[0] = args.workload
         if args.alpha is not None:
             WORKLOAD["alpha"] = args.alpha
     if args.warmup < 3 and args.impl == "gpu":

@@ -66,8 +66,13 @@ typedef enum aao_scheme { AAO_SCHEME_IMPLICIT_LEAPFROG = 0 } aao_scheme;
 /* Precision of the preconditioner application. */
 typedef enum aao_precision {
   AAO_PREC_FP64 = 0,     /* everything in FP64 */
-  AAO_PREC_FP32_IR = 1   /* P_alpha^{-1} in FP32/complex64; operator, MINRES recurrences,
+  AAO_PREC_FP32_IR = 1,  /* P_alpha^{-1} in FP32/complex64; operator, MINRES recurrences,
                             residuals and an outer iterative refinement in FP64 */
+  AAO_PREC_F32X2 = 2     /* the time part of P_alpha^{-1} in double-float arithmetic (pairs
+                            of FP32 numbers, ~48 significant bits, on the FP32 pipes); DSTs,
+                            operator, recurrences and residuals in FP64; no refinement loop
+                            (not a mode of the paper: a GB300 design choice, whose FP64
+                            pipe is 64 times narrower than its FP32 pipes) */
 } aao_precision;
 
 typedef struct aao_opts {

@@ -15,7 +15,7 @@ from typing import List, Optional, Tuple
 __all__ = [
     "AaoError", "AAO_OK", "AAO_EINVAL", "AAO_EUNSUPPORTED", "AAO_ENOMEM", "AAO_ECUDA",
     "AAO_ENOTCONV", "AAO_EBREAKDOWN", "AAO_ESINGULAR", "AAO_EBUSY", "AAO_EPENDING",
-    "AAO_ETIMEOUT", "AAO_PREC_FP64", "AAO_PREC_FP32_IR", "lib", "lib_path", "header_functions",
+    "AAO_ETIMEOUT", "AAO_PREC_FP64", "AAO_PREC_FP32_IR", "AAO_PREC_F32X2", "lib", "lib_path", "header_functions",
     "aao_create", "aao_destroy", "aao_set_coefficient", "aao_autotune", "aao_workspace_bytes", "aao_build_rhs", "aao_apply_op",
     "aao_apply_prec", "aao_apply_dst", "aao_apply_time", "aao_minres_solve", "aao_solve_host",
     "aao_residual_norm", "aao_residual_norm_noalloc",
@@ -26,7 +26,7 @@ __all__ = [
 
 (AAO_OK, AAO_EINVAL, AAO_EUNSUPPORTED, AAO_ENOMEM, AAO_ECUDA, AAO_ENOTCONV, AAO_EBREAKDOWN,
  AAO_ESINGULAR, AAO_EBUSY, AAO_EPENDING, AAO_ETIMEOUT) = range(11)
-AAO_PREC_FP64, AAO_PREC_FP32_IR = 0, 1
+AAO_PREC_FP64, AAO_PREC_FP32_IR, AAO_PREC_F32X2 = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)

@@ -32,13 +32,13 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 enum KClass {
   KC_DST_X64, KC_DST_Y64, KC_DST_Z64, KC_TIME64, KC_DST_X32, KC_DST_Y32, KC_DST_Z32, KC_TIME32,
   KC_YT, KC_YT_DOT, KC_YT_RES, KC_DOT, KC_VUPD, KC_WXUPD, KC_SCAL, KC_RHS, KC_SUB, KC_CAST,
-  KC_AXPY, KC_TABLE, KC_N
+  KC_AXPY, KC_TABLE, KC_TIMEFF, KC_N
 };
 const char* kc_name(int c) {
   static const char* names[KC_N] = {
       "dst_x_f64", "dst_y_f64", "dst_z_f64", "time_f64", "dst_x_f32", "dst_y_f32", "dst_z_f32",
       "time_f32", "yt", "yt_dot", "yt_res", "dot", "vupdate", "wxupdate", "scalars", "rhs", "sub",
-      "cast", "axpy", "spectral_table"};
+      "cast", "axpy", "spectral_table", "time_f32x2"};
   return (c >= 0 && c < KC_N) ? names[c] : "other";
 }
 
@@ -62,6 +62,7 @@ struct aao_handle {
   double* dinv64 = nullptr; double* d264 = nullptr; double2* ab64 = nullptr;
   float2* tw_space32 = nullptr; float* sinw32 = nullptr; float2* tw_time32 = nullptr;
   float* dinv32 = nullptr; float* d232 = nullptr; float2* ab32 = nullptr;
+  dfl2* tw_time_ff = nullptr; dfl* dinv_ff = nullptr; dfl* d2_ff = nullptr; dfl2* ab_ff = nullptr;
   // workspace (nrhs_max * n * m doubles each)
   double* vT = nullptr; double* vv = nullptr; double* vvp = nullptr; double* vz = nullptr;
   double* vzn = nullptr; double* vw = nullptr; double* vwp = nullptr;
@@ -206,6 +207,16 @@ std::vector<float> to_f(const std::vector<double>& v) {
   for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
   return o;
 }
+std::vector<dfl> to_df(const std::vector<double>& v) {
+  std::vector<dfl> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = dfl(v[i]);
+  return o;
+}
+std::vector<dfl2> to_df2(const std::vector<double2>& v) {
+  std::vector<dfl2> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = dfl2{dfl(v[i].x), dfl(v[i].y)};
+  return o;
+}
 
 aao_status check_handle(const aao_handle* h) {
   if (!h) return fail(AAO_EINVAL, "null handle");
@@ -228,6 +239,13 @@ aao_status prec_apply(aao_handle* h, const double* in, double* out, int nrhs, cu
     for (int ax = 1; ax < P.d; ++ax)
       AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
     AAO_KL(h, KC_TIME64, s, launch_time<double>(P, out, out, nrhs, s, &h->launches));
+    for (int ax = P.d - 1; ax >= 0; --ax)
+      AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
+  } else if (h->precision == AAO_PREC_F32X2) {
+    AAO_KL(h, KC_DST_X64, s, launch_dst_axis<double>(P, in, out, 0, nrhs, s, &h->launches));
+    for (int ax = 1; ax < P.d; ++ax)
+      AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
+    AAO_KL(h, KC_TIMEFF, s, launch_time_ff(P, out, out, nrhs, s, &h->launches));
     for (int ax = P.d - 1; ax >= 0; --ax)
       AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
   } else {
@@ -259,6 +277,8 @@ aao_status prec_apply(aao_handle* h, const double* in, double* out, int nrhs, cu
 aao_status time_apply(aao_handle* h, const double* in, double* out, int nrhs, cudaStream_t s) {
   if (h->precision == AAO_PREC_FP64)
     AAO_KL(h, KC_TIME64, s, launch_time<double>(h->P, in, out, nrhs, s, &h->launches));
+  else if (h->precision == AAO_PREC_F32X2)
+    AAO_KL(h, KC_TIMEFF, s, launch_time_ff(h->P, in, out, nrhs, s, &h->launches));
   else
     AAO_KL(h, KC_TIME32, s, launch_time_mixed(h->P, in, out, nrhs, s, &h->launches));
   return AAO_OK;
@@ -708,9 +728,15 @@ aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaSt
     AAO_TRY(upload_on(dinv32, h->dinv32, s));
     AAO_TRY(upload_on(d232, h->d232, s));
   }
+  if (h->precision == AAO_PREC_F32X2) {
+    AAO_TRY(upload_on(to_df(dinv), h->dinv_ff, s));
+    AAO_TRY(upload_on(to_df(d2), h->d2_ff, s));
+  }
   int nb = 0;
   AAO_CK(launch_spectral_table(P, h->d_mu, h->d_wq, h->ab64, fp32 ? h->ab32 : nullptr, h->d_mm, &nb,
                                s, &h->launches));
+  if (h->precision == AAO_PREC_F32X2)
+    AAO_CK(launch_split_df(h->ab64, h->ab_ff, (size_t)(P.n / 2 + 1) * P.npairs * 2, s, &h->launches));
   std::vector<double> mm((size_t)2 * nb);
   AAO_CK(cudaMemcpyAsync(mm.data(), h->d_mm, mm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   AAO_CK(cudaStreamSynchronize(s));
@@ -840,7 +866,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   o.nrhs_max = 1;
   if (opts) o = *opts;
   if (o.nrhs_max < 1) o.nrhs_max = 1;
-  if (o.precision != AAO_PREC_FP64 && o.precision != AAO_PREC_FP32_IR)
+  if (o.precision != AAO_PREC_FP64 && o.precision != AAO_PREC_FP32_IR && o.precision != AAO_PREC_F32X2)
     return fail(AAO_EINVAL, "unknown precision");
   for (int i = 0; i < 4; ++i)
     if (o.reserved[i] != 0) return fail(AAO_EINVAL, "opts.reserved must be zero");
@@ -862,9 +888,14 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   P.c2 = grid->c2;
   P.h = 1.0 / (double)M;
   P.coef = P.c2 * tau * tau / (2.0 * P.h * P.h);
-  if (const char* tv = getenv("AAO_TIME_VARIANT")) {  // tuning override: "v64,v32"
+  if (const char* tv = getenv("AAO_TIME_VARIANT")) {  // tuning override: "v64,v32,vff"
     int a = 0, b = -1;
-    if (sscanf(tv, "%d,%d", &a, &b) >= 1) { P.time_variant64 = a & 7; P.time_variant32 = (b >= 0 ? b : a) & 7; }
+    int c = -1;
+    if (sscanf(tv, "%d,%d,%d", &a, &b, &c) >= 1) {
+      P.time_variant64 = a & 7;
+      P.time_variant32 = (b >= 0 ? b : a) & 7;
+      P.time_variant_ff = (c >= 0 ? c : (b >= 0 ? b : a)) & 7;
+    }
   }
   if (const char* dv = getenv("AAO_DST_VARIANT")) P.dst_variant = atoi(dv) & 1;
 
@@ -896,6 +927,12 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
       (st = h->alloc(&h->d_mm, (size_t)2 * h->mm_blocks)))
     return bail(st);
   const bool fp32 = (o.precision == AAO_PREC_FP32_IR);
+  const bool ff = (o.precision == AAO_PREC_F32X2);
+  if (ff) {
+    if ((st = h->alloc(&h->tw_time_ff, nt)) || (st = h->alloc(&h->dinv_ff, nt)) ||
+        (st = h->alloc(&h->d2_ff, nt)) || (st = h->alloc(&h->ab_ff, tabn)))
+      return bail(st);
+  }
   if (fp32) {
     if ((st = h->alloc(&h->tw_space32, M)) || (st = h->alloc(&h->sinw32, M / 2 + 1)) ||
         (st = h->alloc(&h->tw_time32, nt)) || (st = h->alloc(&h->dinv32, nt)) ||
@@ -958,6 +995,10 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
       P.t32.dinv = h->dinv32; P.t32.d2 = h->d232; P.t32.ab = h->ab32;
       P.t32.cq = (float)(cM / 4.0L);
     }
+    if (ff) {
+      AAO_TRY(upload(to_df2(twT), h->tw_time_ff));
+      P.tff.tw_time = h->tw_time_ff; P.tff.dinv = h->dinv_ff; P.tff.d2 = h->d2_ff; P.tff.ab = h->ab_ff;
+    }
     AAO_TRY(set_params(h, tau, alpha, grid->c2, 0));
     AAO_CK(cudaDeviceSynchronize());
     return AAO_OK;
@@ -966,6 +1007,11 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   if (st != AAO_OK) return bail(st);
   *out = h;
   return AAO_OK;
+}
+
+// the time-kernel variant field used by a precision mode
+static int& tvar(Plan& P, int prec) {
+  return prec == AAO_PREC_FP64 ? P.time_variant64 : prec == AAO_PREC_F32X2 ? P.time_variant_ff : P.time_variant32;
 }
 
 aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
@@ -979,15 +1025,14 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
       bool found = false;
       while (fscanf(fh, "%d %d %d %d %d %d", &d, &N, &n, &pr, &tv, &dv) == 6)
         if (d == P.d && N == P.N && n == P.n && pr == prec) {
-          if (prec == AAO_PREC_FP64) P.time_variant64 = tv & 7;
-          else P.time_variant32 = tv & 7;
+          tvar(P, prec) = tv & 7;
           P.dst_variant = dv & 1;
           found = true;
         }
       fclose(fh);
       if (found) {
         if (chosen) {
-          chosen[0] = prec == AAO_PREC_FP64 ? P.time_variant64 : P.time_variant32;
+          chosen[0] = tvar(P, prec);
           chosen[1] = P.dst_variant;
         }
         AAO_CK(cudaDeviceSynchronize());
@@ -1019,16 +1064,15 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   int best_tv = 0;
   float best_t = 1e30f;
   for (int v = 0; v < 8; ++v) {
-    if (prec == AAO_PREC_FP64) P.time_variant64 = v;
-    else P.time_variant32 = v;
+    tvar(P, prec) = v;
     const float t = timeit([&]() {
       if (prec == AAO_PREC_FP64) launch_time<double>(P, h->vv, h->vz, 1, s, nullptr);
+      else if (prec == AAO_PREC_F32X2) launch_time_ff(P, h->vv, h->vz, 1, s, nullptr);
       else launch_time_mixed(P, h->vv, h->vz, 1, s, nullptr);
     });
     if (t < best_t) { best_t = t; best_tv = v; }
   }
-  if (prec == AAO_PREC_FP64) P.time_variant64 = best_tv;
-  else P.time_variant32 = best_tv;
+  tvar(P, prec) = best_tv;
   int best_dv = 0;
   float best_d = 1e30f;
   for (int v = 0; v < 2; ++v) {

@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "aao.h"
+#include "dfloat.cuh"
 
 namespace aao {
 
@@ -39,6 +40,7 @@ AAO_HD float2 cmulc(float2 a, float2 b) {
 template <typename R> struct Cplx;
 template <> struct Cplx<double> { using T = double2; };
 template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<dfl> { using T = dfl2; };
 
 // ---------------------------------------------------------------------------
 // problem plan: sizes and device tables, built once by aao_create
@@ -60,19 +62,22 @@ struct Plan {
   double tau = 0, alpha = 0, c2 = 0, h = 0;
   double coef = 0;  // c2 tau^2 / (2 h^2): L w = w - coef * (sum of neighbour differences)
   // time-kernel variant per precision: bit 0 = radix-16 stage plan, bit 1 = half-size
-  // tile, bit 2 = interleaved padded shared-memory layout.  Defaults measured on GB300:
-  // FP64 (FP64-pipe bound) radix-16 + half tile, layout immaterial (within 1 %);
-  // FP32 radix-16 + full tile + interleaved layout (bank conflicts dominate otherwise).
-  int time_variant64 = 7, time_variant32 = 5;
+  // tile, bit 2 = interleaved padded shared-memory layout with the table slice staged
+  // in shared memory.  Defaults measured on GB300: FP64 (FP64-pipe bound) radix-16 +
+  // half tile; FP32 radix-16 + full tile + interleaved layout (bank conflicts and
+  // table-load latency dominate otherwise).
+  int time_variant64 = 3, time_variant32 = 5, time_variant_ff = 5;
   // DST stage plan: 0 = radix-4, 1 = radix-16 first
   int dst_variant = 1;
   PrecTables<double> t64;
   PrecTables<float> t32;
+  PrecTables<dfl> tff;  // double-float tables (time pipeline only)
 };
 
 template <typename R> inline const PrecTables<R>& tables(const Plan& P);
 template <> inline const PrecTables<double>& tables<double>(const Plan& P) { return P.t64; }
 template <> inline const PrecTables<float>& tables<float>(const Plan& P) { return P.t32; }
+template <> inline const PrecTables<dfl>& tables<dfl>(const Plan& P) { return P.tff; }
 
 // ---------------------------------------------------------------------------
 // launchers (each returns the CUDA error of its launch and counts launches)
@@ -97,6 +102,11 @@ cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, doub
 // Time pipeline computed in FP32/complex64 on FP64 vectors (conversion in the load and store).
 cudaError_t launch_time_mixed(const Plan& P, const double* in, double* out, int nrhs, cudaStream_t s,
                               uint64_t* nl);
+// Time pipeline computed in double-float arithmetic on FP64 vectors.
+cudaError_t launch_time_ff(const Plan& P, const double* in, double* out, int nrhs, cudaStream_t s,
+                           uint64_t* nl);
+// out[i] = nearest double-float of in[i] (complex), count entries.
+cudaError_t launch_split_df(const double2* in, dfl2* out, size_t count, cudaStream_t s, uint64_t* nl);
 
 cudaError_t launch_build_rhs(const Plan& P, const double* f, const double* psi0, const double* psi1,
                              double* b, int nrhs, cudaStream_t s, uint64_t* nl);

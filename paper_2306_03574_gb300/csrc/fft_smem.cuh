@@ -29,6 +29,8 @@ struct SLay {
   static __device__ __forceinline__ int at(int q, int x) {
     return LAY ? NS * (x + (x >> 4)) + q : q * L + x;
   }
+  // at(q, x + c) - at(q, x), valid when (x mod 16) + (c mod 16) < 16 (no carry into x/16)
+  static constexpr int off(int c) { return LAY ? NS * (c + (c >> 4)) : c; }
   // task -> (sequence q, index j) for a pass with Q tasks per sequence
   template <int Q>
   static __device__ __forceinline__ void split(int task, int& q, int& j) {
@@ -66,80 +68,6 @@ AAO_HD void dft4(C& v0, C& v1, C& v2, C& v3) {
     v1.x = a1.x - a3.y; v1.y = a1.y + a3.x;
     v3.x = a1.x + a3.y; v3.y = a1.y - a3.x;
   }
-}
-
-// One radix-4 Stockham stage with span Ls (sub-transforms of length Ls done).
-template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
-__device__ __forceinline__ void fft_stage4(C* buf, const C* tw, int Ls) {
-  using Y = SLay<L, NS, LAY>;
-  constexpr int Q = L / 4;
-  constexpr int TASKS = NS * Q;
-  static_assert(TASKS % NT == 0, "radix-4 tasks must divide evenly among threads");
-  constexpr int TPT = TASKS / NT;
-  C v[TPT][4];
-#pragma unroll
-  for (int t = 0; t < TPT; ++t) {
-    int q, j;
-    Y::template split<Q>(threadIdx.x + t * NT, q, j);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) v[t][r] = buf[Y::at(q, j + r * Q)];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < TPT; ++t) {
-    int q, j;
-    Y::template split<Q>(threadIdx.x + t * NT, q, j);
-    const int k = j & (Ls - 1);
-    if (Ls > 1) {
-      const int step = (Q / Ls) * k;  // twiddle exponent r*k*L/(4 Ls)
-      v[t][1] = cmul(v[t][1], twid<INV>(tw[step]));
-      v[t][2] = cmul(v[t][2], twid<INV>(tw[2 * step]));
-      v[t][3] = cmul(v[t][3], twid<INV>(tw[3 * step]));
-    }
-    dft4<INV>(v[t][0], v[t][1], v[t][2], v[t][3]);
-    const int o = (j - k) * 4 + k;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) buf[Y::at(q, o + r * Ls)] = v[t][r];
-  }
-  __syncthreads();
-}
-
-// Final radix-2 stage (span L/2).
-template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
-__device__ __forceinline__ void fft_stage2_last(C* buf, const C* tw) {
-  using Y = SLay<L, NS, LAY>;
-  constexpr int Q = L / 2;
-  constexpr int TASKS = NS * Q;
-  static_assert(TASKS % NT == 0, "radix-2 tasks must divide evenly among threads");
-  constexpr int TPT = TASKS / NT;
-  C v[TPT][2];
-#pragma unroll
-  for (int t = 0; t < TPT; ++t) {
-    int q, j;
-    Y::template split<Q>(threadIdx.x + t * NT, q, j);
-    v[t][0] = buf[Y::at(q, j)];
-    v[t][1] = buf[Y::at(q, j + Q)];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int t = 0; t < TPT; ++t) {
-    int q, j;
-    Y::template split<Q>(threadIdx.x + t * NT, q, j);
-    const C b = cmul(v[t][1], twid<INV>(tw[j]));
-    buf[Y::at(q, j)] = cadd(v[t][0], b);
-    buf[Y::at(q, j + Q)] = csub(v[t][0], b);
-  }
-  __syncthreads();
-}
-
-// Full transform of NS sequences of length L by NT threads.  The caller must
-// have synchronised after writing buf; on return buf is synchronised too.
-template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
-__device__ __forceinline__ void fft_block(C* buf, const C* tw) {
-  constexpr int LG = Log2<L>::value;
-#pragma unroll
-  for (int s = 0; s < LG / 2; ++s) fft_stage4<L, NS, NT, INV, LAY>(buf, tw, 1 << (2 * s));
-  if constexpr ((LG & 1) != 0) fft_stage2_last<L, NS, NT, INV, LAY>(buf, tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -222,41 +150,65 @@ AAO_HD void dft_r(C* v) {
   else dft16<INV>(v);
 }
 
-// One radix-RX Stockham stage with span Ls (sub-transforms of length Ls done):
-// task j in [0, L/RX), k = j mod Ls, v_r = x[j + r L/RX], v_r *= w^{r k L/(RX Ls)},
-// DFT_RX, y[(j - k) RX + k + r Ls] = v_r.
-template <int L, int NS, int NT, int RX, bool INV, int LAY = 0, typename C>
-__device__ __forceinline__ void fft_stage_r(C* buf, const C* tw, int Ls) {
+// One radix-RX Stockham stage with span LS (sub-transforms of length LS done):
+// task j in [0, L/RX), k = j mod LS, v_r = x[j + r L/RX], v_r *= w^{r k L/(RX LS)},
+// DFT_RX, y[(j - k) RX + k + r LS] = v_r.  Every thread computes one base index for
+// its reads and one for its writes; the RX elements sit at compile-time offsets from
+// them (in the padded layout the offsets hold because no element of a group crosses
+// a 16-element padding boundary relative to its base: see the static_assert).
+template <int L, int NS, int NT, int RX, bool INV, int LAY, int LS, typename C>
+__device__ __forceinline__ void fft_stage_r(C* buf, const C* tw) {
   using Y = SLay<L, NS, LAY>;
   constexpr int Q = L / RX;
   constexpr int TASKS = NS * Q;
   static_assert(TASKS % NT == 0, "radix tasks must divide evenly among threads");
+  static_assert(LS <= Q && (Q % 16 == 0 || 16 % Q == 0), "read offsets");
+  static_assert(LS % 16 == 0 || RX * LS <= 16, "write offsets");
   constexpr int TPT = TASKS / NT;
   C v[TPT][RX];
 #pragma unroll
   for (int t = 0; t < TPT; ++t) {
     int q, j;
     Y::template split<Q>(threadIdx.x + t * NT, q, j);
+    const C* p = buf + Y::at(q, j);
 #pragma unroll
-    for (int r = 0; r < RX; ++r) v[t][r] = buf[Y::at(q, j + r * Q)];
+    for (int r = 0; r < RX; ++r) v[t][r] = p[Y::off(r * Q)];
   }
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < TPT; ++t) {
     int q, j;
     Y::template split<Q>(threadIdx.x + t * NT, q, j);
-    const int k = j & (Ls - 1);
-    if (Ls > 1) {
-      const int step = (Q / Ls) * k;
+    const int k = j & (LS - 1);
+    if constexpr (LS > 1) {
+      const int step = (Q / LS) * k;
 #pragma unroll
       for (int r = 1; r < RX; ++r) v[t][r] = cmul(v[t][r], twid<INV>(tw[r * step]));
     }
     dft_r<RX, INV>(v[t]);
-    const int o = (j - k) * RX + k;
+    C* o = buf + Y::at(q, (j - k) * RX + k);
 #pragma unroll
-    for (int r = 0; r < RX; ++r) buf[Y::at(q, o + r * Ls)] = v[t][r];
+    for (int r = 0; r < RX; ++r) o[Y::off(r * LS)] = v[t][r];
   }
   __syncthreads();
+}
+
+// Radix-4 stage plan from span LS on, with one radix-2 stage last when log2(L) is odd.
+template <int L, int NS, int NT, bool INV, int LAY, int LS, typename C>
+__device__ __forceinline__ void fft_r4_from(C* buf, const C* tw) {
+  if constexpr (LS * 4 <= L) {
+    fft_stage_r<L, NS, NT, 4, INV, LAY, LS>(buf, tw);
+    fft_r4_from<L, NS, NT, INV, LAY, LS * 4>(buf, tw);
+  } else if constexpr (LS * 2 == L) {
+    fft_stage_r<L, NS, NT, 2, INV, LAY, LS>(buf, tw);
+  }
+}
+
+// Full transform of NS sequences of length L by NT threads (radix-4 plan).  The caller
+// must have synchronised after writing buf; on return buf is synchronised too.
+template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
+__device__ __forceinline__ void fft_block(C* buf, const C* tw) {
+  fft_r4_from<L, NS, NT, INV, LAY, 1>(buf, tw);
 }
 
 // Stage plans with radix-16 first: 64 = 16*4, 128 = 16*8, 256 = 16*16,
@@ -264,22 +216,22 @@ __device__ __forceinline__ void fft_stage_r(C* buf, const C* tw, int Ls) {
 template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
 __device__ __forceinline__ void fft_block16(C* buf, const C* tw) {
   if constexpr (L == 64) {
-    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 4, INV, LAY>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
+    fft_stage_r<L, NS, NT, 4, INV, LAY, 16>(buf, tw);
   } else if constexpr (L == 128) {
-    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 8, INV, LAY>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
+    fft_stage_r<L, NS, NT, 8, INV, LAY, 16>(buf, tw);
   } else if constexpr (L == 256) {
-    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 16);
+    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
+    fft_stage_r<L, NS, NT, 16, INV, LAY, 16>(buf, tw);
   } else if constexpr (L == 512) {
-    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 16);
-    fft_stage_r<L, NS, NT, 2, INV, LAY>(buf, tw, 256);
+    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
+    fft_stage_r<L, NS, NT, 16, INV, LAY, 16>(buf, tw);
+    fft_stage_r<L, NS, NT, 2, INV, LAY, 256>(buf, tw);
   } else {
-    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 1);
-    fft_stage_r<L, NS, NT, 16, INV, LAY>(buf, tw, 16);
-    fft_stage_r<L, NS, NT, 4, INV, LAY>(buf, tw, 256);
+    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
+    fft_stage_r<L, NS, NT, 16, INV, LAY, 16>(buf, tw);
+    fft_stage_r<L, NS, NT, 4, INV, LAY, 256>(buf, tw);
   }
 }
 

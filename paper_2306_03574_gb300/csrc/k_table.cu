@@ -101,7 +101,24 @@ __global__ void __launch_bounds__(256) k_spectral(SpecArgs a, const double* __re
   }
 }
 
+__global__ void k_split_df(const double2* __restrict__ in, dfl2* __restrict__ out, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = dfl2{dfl(v.x), dfl(v.y)};
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_split_df(const double2* in, dfl2* out, size_t count, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  long long nb = ((long long)count + 255) / 256;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  k_split_df<<<(unsigned)nb, 256, 0, s>>>(in, out, (long long)count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_spectral_table(const Plan& P, const double* mu1d, const double2* wq,
                                   double2* ab64, float2* ab32, double* mm, int* nblocks,

@@ -18,12 +18,16 @@
 // Kernel variants (bits of the variant number): bit 0 = FFT stage plan (radix-4
 // or radix-16 first), bit 1 = tile (4096/n mode pairs x 256 threads or 2048/n x
 // 128), bit 2 = shared-memory layout of the batch (sequence-major or interleaved
-// and padded, see fft_smem.cuh).  All variants compute the same values; the
-// translation units k_time64.cu / k_time32.cu instantiate them per precision.
+// and padded, see fft_smem.cuh).  The interleaved variants also stage the CTA's
+// slice of the spectral table in shared memory with asynchronous copies issued
+// before the input load, so both spectral multiplies read it from there and its
+// global-memory latency overlaps the load.  All variants compute the same values;
+// the translation units k_time64.cu / k_time32.cu instantiate them per precision.
 #pragma once
 #include <type_traits>
 
 #include "aao_internal.cuh"
+#include "dfloat.cuh"
 #include "fft_smem.cuh"
 
 namespace aao {
@@ -37,19 +41,50 @@ template <bool CONJ, typename C>
 __device__ __forceinline__ C mix(C A, C B, C Z, C W) {
   if (CONJ) { A.y = -A.y; B.y = -B.y; }
   C Y;
-  Y.x = fma(A.x, Z.x, fma(-A.y, Z.y, fma(B.x, W.x, B.y * W.y)));
-  Y.y = fma(A.x, Z.y, fma(A.y, Z.x, fma(B.y, W.x, -(B.x * W.y))));
+  Y.x = fmadd(A.x, Z.x, fmadd(-A.y, Z.y, fmadd(B.x, W.x, B.y * W.y)));
+  Y.y = fmadd(A.x, Z.y, fmadd(A.y, Z.x, fmadd(B.y, W.x, -(B.x * W.y))));
   return Y;
 }
 
-template <bool CONJ, int L, int NS, int NT, int LAY, typename C>
-__device__ __forceinline__ void mix_pass(C* cbuf, const C* __restrict__ ab, int npairs, int p0) {
+// 16-byte asynchronous global -> shared copy; bytes past src_bytes are zero-filled
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Copy the CTA's table slice ab[k][p0 + q][A|B], k = 0..L/2, q < NS, into tab[(k NS + q) 2 + {0,1}]
+// (rows past the last mode pair are zero-filled).  Each (k, q) entry is 2 sizeof(C) bytes,
+// a whole number of 16-byte chunks starting on a 16-byte boundary.
+template <int L, int NS, int NT, typename C>
+__device__ __forceinline__ void stage_table(C* tab, const C* __restrict__ ab, int npairs, int p0) {
+  constexpr int H = L / 2;
+  constexpr int CH = (2 * (int)sizeof(C)) / 16;  // 16-byte chunks per entry
+  for (int task = threadIdx.x; task < NS * (H + 1) * CH; task += NT) {
+    const int c = task % CH, e = task / CH;
+    const int q = e % NS, k = e / NS;
+    const bool ok = p0 + q < npairs;
+    const C* src = ok ? ab + ((long long)k * npairs + p0 + q) * 2 : ab;
+    cp_async16(reinterpret_cast<char*>(tab + (long long)e * 2) + 16 * c,
+               reinterpret_cast<const char*>(src) + 16 * c, ok ? 16 : 0);
+  }
+  cp_async_commit();
+}
+
+// Spectral multiply of every sequence of the tile; the (A, B) entries come from the
+// staged slice tab when STAGED, else from the table in global memory.
+template <bool CONJ, int L, int NS, int NT, int LAY, bool STAGED, typename C>
+__device__ __forceinline__ void mix_pass(C* cbuf, const C* __restrict__ ab, const C* tab, int npairs, int p0) {
   using Y = SLay<L, NS, LAY>;
   constexpr int H = L / 2;
   for (int task = threadIdx.x; task < NS * (H + 1); task += NT) {
     const int q = task % NS, k = task / NS;
     C A, B;
-    if (p0 + q < npairs) {  // tiles may extend past the last mode pair (zero data there)
+    if constexpr (STAGED) {
+      A = tab[2 * task];
+      B = tab[2 * task + 1];
+    } else if (p0 + q < npairs) {  // tiles may extend past the last mode pair (zero data there)
       const long long row = ((long long)k * npairs + p0 + q) * 2;
       A = ab[row];
       B = ab[row + 1];
@@ -81,16 +116,20 @@ template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
   using Y = SLay<L, NS, LAY>;
+  constexpr bool STAGED = LAY == 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cbuf = reinterpret_cast<C*>(smem_raw);
-  C* tw = cbuf + Y::size;
+  C* tab = cbuf + Y::size;                           // staged table slice (STAGED only)
+  C* tw = tab + (STAGED ? 2 * NS * (L / 2 + 1) : 0);
   R* dinv = reinterpret_cast<R*>(tw + L);
   R* d2 = dinv + L;
 
   const int tid = threadIdx.x;
   const int m = a.m;
   const int s0 = blockIdx.x * (2 * NS);
+  const int p0 = blockIdx.x * NS;
   const long long rb = (long long)blockIdx.y * L * m;
+  if constexpr (STAGED) stage_table<L, NS, NT>(tab, tb.ab, a.npairs, p0);
   for (int i = tid; i < L; i += NT) {
     tw[i] = tb.tw_time[i];
     dinv[i] = tb.dinv[i];
@@ -109,11 +148,11 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
     z.y = (sa + 1 < m) ? R(p[1]) * di : R(0);
     cbuf[Y::at(q, t)] = z;
   }
+  if constexpr (STAGED) cp_async_wait_all();
   __syncthreads();
 
-  const int p0 = blockIdx.x * NS;
   fft_run<FFTV, L, NS, NT, false, LAY>(cbuf, tw);
-  mix_pass<false, L, NS, NT, LAY>(cbuf, tb.ab, a.npairs, p0);
+  mix_pass<false, L, NS, NT, LAY, STAGED>(cbuf, tb.ab, tab, a.npairs, p0);
   fft_run<FFTV, L, NS, NT, true, LAY>(cbuf, tw);
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
@@ -125,7 +164,7 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
   }
   __syncthreads();
   fft_run<FFTV, L, NS, NT, false, LAY>(cbuf, tw);
-  mix_pass<true, L, NS, NT, LAY>(cbuf, tb.ab, a.npairs, p0);
+  mix_pass<true, L, NS, NT, LAY, STAGED>(cbuf, tb.ab, tab, a.npairs, p0);
   fft_run<FFTV, L, NS, NT, true, LAY>(cbuf, tw);
 
   // scale by D^{-1} and store
@@ -144,7 +183,8 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
 template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY>
 static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
-  const size_t smem = sizeof(C) * (SLay<L, NS, LAY>::size + L) + 2 * sizeof(R) * L;
+  const size_t smem = sizeof(C) * (SLay<L, NS, LAY>::size + (LAY ? 2 * NS * (L / 2 + 1) : 0) + L) +
+                      2 * sizeof(R) * L;
   TimeArgs a;
   a.m = P.m;
   a.n = P.n;
@@ -158,7 +198,9 @@ static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int n
 
 template <typename R, typename TIO, int L>
 static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
-  const int v = std::is_same<R, double>::value ? P.time_variant64 : P.time_variant32;
+  const int v = std::is_same<R, double>::value  ? P.time_variant64
+                : std::is_same<R, float>::value ? P.time_variant32
+                                                : P.time_variant_ff;
   switch (v & 7) {
     case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0, 0>(P, in, out, nrhs, s);
     case 1: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 0>(P, in, out, nrhs, s);
