@@ -55,7 +55,19 @@ WORKLOADS = {
                                precision="fp64", varcoef=True),
     "2d255_varcoef_mixed": dict(d=2, N=255, nt=256, alpha=1e-3, rtol=1e-8, maxit=300, seed=0, nrhs=1,
                                 precision="fp32", varcoef=True),
+    # double-float time pipeline (pairs of FP32 numbers on the FP32 pipes), FP64 elsewhere
+    "2d255_f32x2": dict(d=2, N=255, nt=256, alpha=1e-6, rtol=1e-8, maxit=100, seed=2, nrhs=1,
+                        precision="f32x2"),
+    "2d511_f32x2": dict(d=2, N=511, nt=512, alpha=1e-6, rtol=1e-8, maxit=100, seed=3, nrhs=1,
+                        precision="f32x2"),
+    "3d127x8_f32x2": dict(d=3, N=127, nt=128, alpha=1e-6, rtol=1e-8, maxit=100, seed=4, nrhs=8,
+                          precision="f32x2"),
 }
+# FP32 operations per FP64-equivalent flop of the double-word arithmetic: a sloppy
+# double-word addition takes 11 FP32 flops (2Sum 6, low-part sum 1, fold-in 1,
+# Fast2Sum 3), a double-word product 10 (product 1, three FMAs 6, Fast2Sum 3); an FFT's
+# flop count is 60 % additions and 40 % multiplications (radix-2 butterfly: 6 + 4).
+DW_FP32_FLOPS_PER_FLOP = 0.6 * 11 + 0.4 * 10
 WORKLOAD = dict(WORKLOADS["2d255_fp64"])
 WORKLOAD_NAME = ["2d255_fp64"]
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
@@ -90,7 +102,7 @@ def algorithmic_bytes(cls: str, d: int, N: int, nt: int, unknowns: int, vec_byte
     right-hand sides)."""
     m = N ** d
     if cls.startswith("time"):
-        csize = 16 if cls.endswith("f64") else 8
+        csize = 8 if cls == "time_f32" else 16
         return 2 * vec_bytes * unknowns + (nt // 2 + 1) * ((m + 1) // 2) * 2 * csize
     if cls.startswith("dst"):
         return 2 * vec_bytes * unknowns
@@ -422,7 +434,8 @@ def run_gpu(args, world, rank, local):
     psi1 = torch.from_numpy(p1np).to(dev)
     b = torch.empty((nrhs, p.nt, p.m), dtype=torch.float64, device=dev)
     x = torch.empty_like(b)
-    prec = aao.AAO_PREC_FP64 if WORKLOAD["precision"] == "fp64" else aao.AAO_PREC_FP32_IR
+    prec = {"fp64": aao.AAO_PREC_FP64, "fp32": aao.AAO_PREC_FP32_IR, "f32x2": aao.AAO_PREC_F32X2}[
+        WORKLOAD["precision"]]
     if varcoef:
         afun = p.meta["a"]
         s = aao.Solver(d, p.N, p.nt, p.tau, p.alpha, c2=W.grid_mean(afun, d, N), precision=prec,
@@ -488,7 +501,10 @@ def run_gpu(args, world, rank, local):
 
     def roof(cls):
         fl = algorithmic_flops(cls, d, p.N, p.nt, unknowns)
-        by = algorithmic_bytes(cls, d, p.N, p.nt, unknowns, 8 if cls.endswith("f64") or cls.startswith("yt") else vb32)
+        if cls == "time_f32x2":  # counted as the FP32 operations of the double-word algorithms
+            fl *= DW_FP32_FLOPS_PER_FLOP
+        by = algorithmic_bytes(cls, d, p.N, p.nt, unknowns,
+                               8 if cls.endswith("f64") or cls.startswith("yt") or cls == "time_f32x2" else vb32)
         alu_peak = FP64_PEAK_TFLOPS if cls.endswith("f64") or cls.startswith("yt") else FP32_PEAK_TFLOPS
         t = kern[cls]["avg_ms"] / 1e3
         # the binding roofline: whichever of the ALU and HBM times is longer
@@ -499,7 +515,10 @@ def run_gpu(args, world, rank, local):
                     "peak_note": ("FP64" if alu_peak == FP64_PEAK_TFLOPS else "FP32") +
                                  " CUDA-core peak from unit counts and clocks: 152 SMs x " +
                                  ("2 DFMA" if alu_peak == FP64_PEAK_TFLOPS else "128 FFMA") +
-                                 "/clk x 2 flop x 2.07 GHz"}
+                                 "/clk x 2 flop x 2.07 GHz" +
+                                 ("; achieved counts the FP32 flops of the double-word algorithms "
+                                  "(%.1f per FP64-equivalent flop)" % DW_FP32_FLOPS_PER_FLOP
+                                  if cls == "time_f32x2" else "")}
         return {"kernel": cls, "bound": "hbm", "achieved": by / t / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": by / t / 1e9 / hbm, "flops_per_launch": fl, "bytes_per_launch": by,
                 "peak_note": "measured copy bandwidth (of measured)"}
@@ -516,7 +535,7 @@ def run_gpu(args, world, rank, local):
             kern[k].update(bound=r["bound"], achieved=r["achieved"], unit=r["unit"], frac=r["frac"])
     # preconditioner application as a whole, against HBM (16 B per unknown in + out)
     prec_cls = [k for k in kern if k.startswith("dst") or k.startswith("time") or k == "cast"]
-    applies = kern.get("time_f64", kern.get("time_f32", {})).get("launches", 0)
+    applies = kern.get("time_f64", kern.get("time_f32", kern.get("time_f32x2", {}))).get("launches", 0)
     prec_ms = sum(kern[k]["total_ms"] for k in prec_cls) / max(applies, 1)
     prec = {"ms_per_apply": prec_ms, "algorithmic_bytes": 16 * unknowns,
             "hbm_gbs": 16 * unknowns / (prec_ms / 1e3) / 1e9 if prec_ms else None}
@@ -577,12 +596,14 @@ def run_gpu(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if WORKLOAD["precision"] == "fp64" else "f32+f64",
+            "dtype": {"fp64": "f64", "fp32": "f32+f64", "f32x2": "f32x2+f64"}[WORKLOAD["precision"]],
             "data": "synthetic", "config": workload_config(unknowns, args.workload),
             "iters_per_solve": it, "relres_true": relres,
             "unknown_iters_per_s": world * unknowns * it * args.steps / (ms_max / 1e3),
-            "dtype_note": ("f64 throughout" if WORKLOAD["precision"] == "fp64" else
-                           "f32/complex64 preconditioner; f64 operator, MINRES recurrences and refinement"),
+            "dtype_note": {"fp64": "f64 throughout",
+                           "fp32": "f32/complex64 preconditioner; f64 operator, MINRES recurrences and refinement",
+                           "f32x2": "time part of the preconditioner in double-float (FP32 pairs, ~47 bits); "
+                                    "f64 DSTs, operator and MINRES recurrences"}[WORKLOAD["precision"]],
             "prec_apply": prec, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "kernels": kern, "kernel_variants": variants,
         }

@@ -21,17 +21,17 @@ def main():
     ap.add_argument("--nt", type=int, default=256)
     ap.add_argument("--alpha", type=float, default=1e-6)
     ap.add_argument("--nrhs", type=int, default=1)
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "f32x2"], default="fp64")
     ap.add_argument("--what", choices=["prec", "time", "dst", "op", "solve"], default="prec")
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--time-variant", type=int, default=None, help="time-kernel variant 0..7")
     ap.add_argument("--dst-variant", type=int, default=None, help="DST variant 0..1")
     a = ap.parse_args()
     if a.time_variant is not None:
-        os.environ["AAO_TIME_VARIANT"] = f"{a.time_variant},{a.time_variant}"
+        os.environ["AAO_TIME_VARIANT"] = f"{a.time_variant},{a.time_variant},{a.time_variant}"
     if a.dst_variant is not None:
         os.environ["AAO_DST_VARIANT"] = str(a.dst_variant)
-    prec = aao.AAO_PREC_FP64 if a.precision == "fp64" else aao.AAO_PREC_FP32_IR
+    prec = {"fp64": aao.AAO_PREC_FP64, "fp32": aao.AAO_PREC_FP32_IR, "f32x2": aao.AAO_PREC_F32X2}[a.precision]
     m = a.N ** a.d
     rng = np.random.default_rng(1)
     x = torch.from_numpy(rng.standard_normal((a.nrhs, a.nt, m))).cuda()
