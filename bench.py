@@ -501,10 +501,10 @@ def run_gpu(args, world, rank, local):
 
     def roof(cls):
         fl = algorithmic_flops(cls, d, p.N, p.nt, unknowns)
-        if cls == "time_f32x2":  # counted as the FP32 operations of the double-word algorithms
+        if cls.endswith("f32x2"):  # counted as the FP32 operations of the double-word algorithms
             fl *= DW_FP32_FLOPS_PER_FLOP
         by = algorithmic_bytes(cls, d, p.N, p.nt, unknowns,
-                               8 if cls.endswith("f64") or cls.startswith("yt") or cls == "time_f32x2" else vb32)
+                               8 if cls.endswith("f64") or cls.startswith("yt") or cls.endswith("f32x2") else vb32)
         alu_peak = FP64_PEAK_TFLOPS if cls.endswith("f64") or cls.startswith("yt") else FP32_PEAK_TFLOPS
         t = kern[cls]["avg_ms"] / 1e3
         # the binding roofline: whichever of the ALU and HBM times is longer
@@ -518,7 +518,7 @@ def run_gpu(args, world, rank, local):
                                  "/clk x 2 flop x 2.07 GHz" +
                                  ("; achieved counts the FP32 flops of the double-word algorithms "
                                   "(%.1f per FP64-equivalent flop)" % DW_FP32_FLOPS_PER_FLOP
-                                  if cls == "time_f32x2" else "")}
+                                  if cls.endswith("f32x2") else "")}
         return {"kernel": cls, "bound": "hbm", "achieved": by / t / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": by / t / 1e9 / hbm, "flops_per_launch": fl, "bytes_per_launch": by,
                 "peak_note": "measured copy bandwidth (of measured)"}
@@ -602,8 +602,8 @@ def run_gpu(args, world, rank, local):
             "unknown_iters_per_s": world * unknowns * it * args.steps / (ms_max / 1e3),
             "dtype_note": {"fp64": "f64 throughout",
                            "fp32": "f32/complex64 preconditioner; f64 operator, MINRES recurrences and refinement",
-                           "f32x2": "time part of the preconditioner in double-float (FP32 pairs, ~47 bits); "
-                                    "f64 DSTs, operator and MINRES recurrences"}[WORKLOAD["precision"]],
+                           "f32x2": "preconditioner and DSTs in double-float (FP32 pairs, ~47 bits) on f64 "
+                                    "vectors; f64 operator, MINRES recurrences and residuals"}[WORKLOAD["precision"]],
             "prec_apply": prec, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "kernels": kern, "kernel_variants": variants,
         }

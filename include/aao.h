@@ -68,11 +68,12 @@ typedef enum aao_precision {
   AAO_PREC_FP64 = 0,     /* everything in FP64 */
   AAO_PREC_FP32_IR = 1,  /* P_alpha^{-1} in FP32/complex64; operator, MINRES recurrences,
                             residuals and an outer iterative refinement in FP64 */
-  AAO_PREC_F32X2 = 2     /* the time part of P_alpha^{-1} in double-float arithmetic (pairs
-                            of FP32 numbers, ~48 significant bits, on the FP32 pipes); DSTs,
-                            operator, recurrences and residuals in FP64; no refinement loop
-                            (not a mode of the paper: a GB300 design choice, whose FP64
-                            pipe is 64 times narrower than its FP32 pipes) */
+  AAO_PREC_F32X2 = 2     /* P_alpha^{-1} (DSTs and time part) and the DSTs of the solve in
+                            double-float arithmetic (pairs of FP32 numbers, ~47 significant
+                            bits, on the FP32 pipes) on FP64 vectors; operator, recurrences and
+                            residuals in FP64; no refinement loop (not a mode of the paper: a
+                            GB300 design choice, whose FP64 pipe issues 64 times fewer
+                            operations per clock than its FP32 pipes) */
 } aao_precision;
 
 typedef struct aao_opts {
@@ -166,7 +167,8 @@ aao_status aao_apply_prec(aao_handle* h, const double* r, double* z, int nrhs, v
 /* y = (I_n (x) U) x with U = S (x) ... (x) S the orthonormal multi-dimensional
  * DST-I (Section 2.3: on a uniform grid the eigenvector matrix U of L is the
  * DST); U = U^T = U^{-1}.  This is the spatial part of P_alpha^{-1}, exposed on
- * its own.  x, y: nrhs x n x m, may be equal.  FP64.  Errors: AAO_EINVAL, AAO_ECUDA. */
+ * its own.  x, y: nrhs x n x m FP64 vectors, may be equal; FP64 arithmetic, or
+ * double-float for an AAO_PREC_F32X2 handle.  Errors: AAO_EINVAL, AAO_ECUDA. */
 aao_status aao_apply_dst(aao_handle* h, const double* x, double* y, int nrhs, void* stream);
 
 /* The time part of P_alpha^{-1} on DST coefficients: for every spatial mode j

@@ -32,13 +32,13 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 enum KClass {
   KC_DST_X64, KC_DST_Y64, KC_DST_Z64, KC_TIME64, KC_DST_X32, KC_DST_Y32, KC_DST_Z32, KC_TIME32,
   KC_YT, KC_YT_DOT, KC_YT_RES, KC_DOT, KC_VUPD, KC_WXUPD, KC_SCAL, KC_RHS, KC_SUB, KC_CAST,
-  KC_AXPY, KC_TABLE, KC_TIMEFF, KC_N
+  KC_AXPY, KC_TABLE, KC_TIMEFF, KC_DST_XFF, KC_DST_YFF, KC_DST_ZFF, KC_N
 };
 const char* kc_name(int c) {
   static const char* names[KC_N] = {
       "dst_x_f64", "dst_y_f64", "dst_z_f64", "time_f64", "dst_x_f32", "dst_y_f32", "dst_z_f32",
       "time_f32", "yt", "yt_dot", "yt_res", "dot", "vupdate", "wxupdate", "scalars", "rhs", "sub",
-      "cast", "axpy", "spectral_table", "time_f32x2"};
+      "cast", "axpy", "spectral_table", "time_f32x2", "dst_x_f32x2", "dst_y_f32x2", "dst_z_f32x2"};
   return (c >= 0 && c < KC_N) ? names[c] : "other";
 }
 
@@ -63,6 +63,7 @@ struct aao_handle {
   float2* tw_space32 = nullptr; float* sinw32 = nullptr; float2* tw_time32 = nullptr;
   float* dinv32 = nullptr; float* d232 = nullptr; float2* ab32 = nullptr;
   dfl2* tw_time_ff = nullptr; dfl* dinv_ff = nullptr; dfl* d2_ff = nullptr; dfl2* ab_ff = nullptr;
+  dfl2* tw_space_ff = nullptr; dfl* sinw_ff = nullptr;
   // workspace (nrhs_max * n * m doubles each)
   double* vT = nullptr; double* vv = nullptr; double* vvp = nullptr; double* vz = nullptr;
   double* vzn = nullptr; double* vw = nullptr; double* vwp = nullptr;
@@ -242,12 +243,12 @@ aao_status prec_apply(aao_handle* h, const double* in, double* out, int nrhs, cu
     for (int ax = P.d - 1; ax >= 0; --ax)
       AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
   } else if (h->precision == AAO_PREC_F32X2) {
-    AAO_KL(h, KC_DST_X64, s, launch_dst_axis<double>(P, in, out, 0, nrhs, s, &h->launches));
+    AAO_KL(h, KC_DST_XFF, s, launch_dst_axis_ff(P, in, out, 0, nrhs, s, &h->launches));
     for (int ax = 1; ax < P.d; ++ax)
-      AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
+      AAO_KL(h, KC_DST_XFF + ax, s, launch_dst_axis_ff(P, out, out, ax, nrhs, s, &h->launches));
     AAO_KL(h, KC_TIMEFF, s, launch_time_ff(P, out, out, nrhs, s, &h->launches));
     for (int ax = P.d - 1; ax >= 0; --ax)
-      AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(P, out, out, ax, nrhs, s, &h->launches));
+      AAO_KL(h, KC_DST_XFF + ax, s, launch_dst_axis_ff(P, out, out, ax, nrhs, s, &h->launches));
   } else {
     const size_t cnt = (size_t)nrhs * h->vlen();
     if (!h->f32) AAO_TRY(h->alloc(&h->f32, (size_t)h->nrhs_max * h->vlen()));  // first FP32 apply_prec
@@ -284,8 +285,15 @@ aao_status time_apply(aao_handle* h, const double* in, double* out, int nrhs, cu
   return AAO_OK;
 }
 
-// (I (x) U) in -> out (FP64; out may equal in)
+// (I (x) U) in -> out (FP64 vectors; out may equal in); double-float arithmetic for an
+// AAO_PREC_F32X2 handle, FP64 otherwise
 aao_status dst_apply(aao_handle* h, const double* in, double* out, int nrhs, cudaStream_t s) {
+  if (h->precision == AAO_PREC_F32X2) {
+    AAO_KL(h, KC_DST_XFF, s, launch_dst_axis_ff(h->P, in, out, 0, nrhs, s, &h->launches));
+    for (int ax = 1; ax < h->P.d; ++ax)
+      AAO_KL(h, KC_DST_XFF + ax, s, launch_dst_axis_ff(h->P, out, out, ax, nrhs, s, &h->launches));
+    return AAO_OK;
+  }
   AAO_KL(h, KC_DST_X64, s, launch_dst_axis<double>(h->P, in, out, 0, nrhs, s, &h->launches));
   for (int ax = 1; ax < h->P.d; ++ax)
     AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(h->P, out, out, ax, nrhs, s, &h->launches));
@@ -929,7 +937,8 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   const bool fp32 = (o.precision == AAO_PREC_FP32_IR);
   const bool ff = (o.precision == AAO_PREC_F32X2);
   if (ff) {
-    if ((st = h->alloc(&h->tw_time_ff, nt)) || (st = h->alloc(&h->dinv_ff, nt)) ||
+    if ((st = h->alloc(&h->tw_space_ff, M)) || (st = h->alloc(&h->sinw_ff, M / 2 + 1)) ||
+        (st = h->alloc(&h->tw_time_ff, nt)) || (st = h->alloc(&h->dinv_ff, nt)) ||
         (st = h->alloc(&h->d2_ff, nt)) || (st = h->alloc(&h->ab_ff, tabn)))
       return bail(st);
   }
@@ -997,7 +1006,11 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     }
     if (ff) {
       AAO_TRY(upload(to_df2(twT), h->tw_time_ff));
+      AAO_TRY(upload(to_df2(twS), h->tw_space_ff));
+      AAO_TRY(upload(to_df(sinw), h->sinw_ff));
       P.tff.tw_time = h->tw_time_ff; P.tff.dinv = h->dinv_ff; P.tff.d2 = h->d2_ff; P.tff.ab = h->ab_ff;
+      P.tff.tw_space = h->tw_space_ff; P.tff.sinw = h->sinw_ff;
+      P.tff.cq = dfl((double)(cM / 4.0L));
     }
     AAO_TRY(set_params(h, tau, alpha, grid->c2, 0));
     AAO_CK(cudaDeviceSynchronize());
@@ -1077,7 +1090,10 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   float best_d = 1e30f;
   for (int v = 0; v < 2; ++v) {
     P.dst_variant = v;
-    const float t = timeit([&]() { launch_dst_axis<double>(P, h->vv, h->vz, 0, 1, s, nullptr); });
+    const float t = timeit([&]() {
+      if (prec == AAO_PREC_F32X2) launch_dst_axis_ff(P, h->vv, h->vz, 0, 1, s, nullptr);
+      else launch_dst_axis<double>(P, h->vv, h->vz, 0, 1, s, nullptr);
+    });
     if (t < best_d) { best_d = t; best_dv = v; }
   }
   P.dst_variant = best_dv;
@@ -1185,11 +1201,7 @@ aao_status aao_apply_prec(aao_handle* h, const double* r, double* z, int nrhs, v
 aao_status aao_apply_dst(aao_handle* h, const double* x, double* y, int nrhs, void* stream) {
   AAO_TRY(check_call(h, nrhs));
   if (!x || !y) return fail(AAO_EINVAL, "null pointer");
-  cudaStream_t s = (cudaStream_t)stream;
-  AAO_KL(h, KC_DST_X64, s, launch_dst_axis<double>(h->P, x, y, 0, nrhs, s, &h->launches));
-  for (int ax = 1; ax < h->P.d; ++ax)
-    AAO_KL(h, KC_DST_X64 + ax, s, launch_dst_axis<double>(h->P, y, y, ax, nrhs, s, &h->launches));
-  return AAO_OK;
+  return dst_apply(h, x, y, nrhs, (cudaStream_t)stream);
 }
 
 aao_status aao_apply_time(aao_handle* h, const double* x, double* y, int nrhs, void* stream) {

@@ -71,7 +71,7 @@ struct Plan {
   int dst_variant = 1;
   PrecTables<double> t64;
   PrecTables<float> t32;
-  PrecTables<dfl> tff;  // double-float tables (time pipeline only)
+  PrecTables<dfl> tff;  // double-float tables
 };
 
 template <typename R> inline const PrecTables<R>& tables(const Plan& P);
@@ -102,6 +102,9 @@ cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, doub
 // Time pipeline computed in FP32/complex64 on FP64 vectors (conversion in the load and store).
 cudaError_t launch_time_mixed(const Plan& P, const double* in, double* out, int nrhs, cudaStream_t s,
                               uint64_t* nl);
+// Spatial DST-I computed in double-float arithmetic on FP64 vectors.
+cudaError_t launch_dst_axis_ff(const Plan& P, const double* in, double* out, int axis, int nrhs,
+                               cudaStream_t s, uint64_t* nl);
 // Time pipeline computed in double-float arithmetic on FP64 vectors.
 cudaError_t launch_time_ff(const Plan& P, const double* in, double* out, int nrhs, cudaStream_t s,
                            uint64_t* nl);

@@ -22,13 +22,17 @@
 
 namespace aao {
 
+struct dfl;
+__host__ __device__ __forceinline__ dfl split_double(double x);
+__host__ __device__ __forceinline__ double join_double(float hi, float lo);
+
 struct dfl {
   float hi, lo;
   __host__ __device__ __forceinline__ dfl() : hi(0.f), lo(0.f) {}
   __host__ __device__ __forceinline__ dfl(float h, float l) : hi(h), lo(l) {}
-  // nearest double-float to x (hi = x rounded to FP32, lo = the remainder rounded)
-  __host__ __device__ __forceinline__ dfl(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
-  __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+  // a double-float within 2^-48 relative of x (hi + lo, |lo| <= ulp(hi)/2)
+  __host__ __device__ __forceinline__ dfl(double x);
+  __host__ __device__ __forceinline__ explicit operator double() const { return join_double(hi, lo); }
 };
 
 __host__ __device__ __forceinline__ dfl fast_two_sum(float a, float b) {
@@ -36,6 +40,66 @@ __host__ __device__ __forceinline__ dfl fast_two_sum(float a, float b) {
   const float t = b - (s - a);
   return dfl(s, t);
 }
+
+// Conversions between double and double-float.  Device code assembles the FP32 parts
+// from the bit fields of the double with integer and FP32 operations, because GB300's
+// narrow FP64 pipe also executes the FP64 <-> FP32 conversion instructions: with them a
+// double-float transform spends half its time converting its input and output.
+//   split: x = (-1)^s 2^E 1.m (52-bit m).  a = x with m truncated to 23 bits (an FP32
+//   number, exact); the remainder x - a = (-1)^s r 2^(E-52) with the 29-bit integer
+//   r = low bits of m, written as (r >> 6) 2^(E-46) + (r & 63) 2^(E-52): both integers
+//   convert exactly by the 2^23 bias trick, the powers of two are exact FP32 scalings,
+//   and one FMA rounds their sum; Fast2Sum renormalises (a, remainder).  Zero (and the
+//   subnormal doubles) give 0; other exponents outside [-70, 120] take the conversion
+//   instructions.
+//   join: each FP32 part becomes a double by re-biasing its exponent and shifting its
+//   mantissa (exact), then one FP64 addition.
+__host__ __device__ __forceinline__ dfl split_double(double x) {
+#ifdef __CUDA_ARCH__
+  const unsigned hw = (unsigned)__double2hiint(x);
+  const unsigned lw = (unsigned)__double2loint(x);
+  const int E = (int)((hw >> 20) & 0x7FFu) - 1023;
+  if (E == -1023) return dfl();  // zero (and subnormal doubles, far below the FP32 range)
+  if (E < -70 || E > 120) {
+    const float h = __double2float_rn(x);
+    return dfl(h, __double2float_rn(x - (double)h));
+  }
+  const unsigned sign = hw & 0x80000000u;
+  const float a = __uint_as_float(sign | ((unsigned)(E + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  const unsigned r = lw & 0x1FFFFFFFu;
+  const float rh = __uint_as_float(0x4B000000u | (r >> 6)) - 8388608.f;
+  const float rl = __uint_as_float(0x4B000000u | (r & 63u)) - 8388608.f;
+  const float s1 = __uint_as_float((unsigned)(E - 46 + 127) << 23);
+  const float s0 = __uint_as_float((unsigned)(E - 52 + 127) << 23);
+  float l = fmaf(rh, s1, rl * s0);
+  if (sign) l = -l;
+  return fast_two_sum(a, l);
+#else
+  const float h = (float)x;
+  return dfl(h, (float)(x - (double)h));
+#endif
+}
+
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ double float_to_double_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  if (e == 0u || e == 0xFFu) return (double)f;  // subnormal, inf, nan
+  const unsigned hw = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hw, (int)((u & 7u) << 29));
+}
+#endif
+
+__host__ __device__ __forceinline__ double join_double(float hi, float lo) {
+#ifdef __CUDA_ARCH__
+  return float_to_double_bits(hi) + float_to_double_bits(lo);
+#else
+  return (double)hi + (double)lo;
+#endif
+}
+
+__host__ __device__ __forceinline__ dfl::dfl(double x) : hi(0.f), lo(0.f) { *this = split_double(x); }
 
 __host__ __device__ __forceinline__ dfl two_sum(float a, float b) {
   const float s = a + b;

@@ -78,6 +78,11 @@ AAO_HD void dft4(C& v0, C& v1, C& v2, C& v3) {
 // ---------------------------------------------------------------------------
 
 // v * exp(-+ 2 pi i m / 16) for the constant m (INV: the conjugate root)
+// A compile-time constant in the arithmetic type R (for double-float the split is
+// written out so that it folds at compile time instead of converting at run time).
+template <typename R> AAO_HD R real_const(double x) { return R(x); }
+template <> AAO_HD dfl real_const<dfl>(double x) { return dfl((float)x, (float)(x - (double)(float)x)); }
+
 template <int M, bool INV, typename C>
 AAO_HD C w16(C v) {
   using R = decltype(v.x);
@@ -85,23 +90,24 @@ AAO_HD C w16(C v) {
   constexpr double s1 = 0.38268343236508977173;  // sin(pi/8)
   constexpr double h = 0.70710678118654752440;   // sqrt(2)/2
   constexpr int m = M & 15;
-  double cr, ci;  // exp(-2 pi i m/16) = cos - i sin
-  switch (m) {
-    case 0: return v;
-    case 1: cr = c1; ci = -s1; break;
-    case 2: cr = h; ci = -h; break;
-    case 3: cr = s1; ci = -c1; break;
-    case 4: { C o; if (!INV) { o.x = v.y; o.y = -v.x; } else { o.x = -v.y; o.y = v.x; } return o; }
-    case 5: cr = -s1; ci = -c1; break;
-    case 6: cr = -h; ci = -h; break;
-    case 7: cr = -c1; ci = -s1; break;
-    case 8: { C o; o.x = -v.x; o.y = -v.y; return o; }
-    case 9: cr = -c1; ci = s1; break;
-    default: cr = 0; ci = 0; break;
+  if constexpr (m == 0) {
+    return v;
+  } else if constexpr (m == 4) {
+    C o;
+    if (!INV) { o.x = v.y; o.y = -v.x; } else { o.x = -v.y; o.y = v.x; }
+    return o;
+  } else if constexpr (m == 8) {
+    C o; o.x = -v.x; o.y = -v.y;
+    return o;
+  } else {
+    // exp(-2 pi i m/16) = cos - i sin
+    constexpr double cr = m == 1 ? c1 : m == 2 ? h : m == 3 ? s1 : m == 5 ? -s1 : m == 6 ? -h : m == 7 ? -c1 : -c1;
+    constexpr double ci0 = m == 1 ? -s1 : m == 2 ? -h : m == 3 ? -c1 : m == 5 ? -c1 : m == 6 ? -h : m == 7 ? -s1 : s1;
+    constexpr double ci = INV ? -ci0 : ci0;
+    static_assert(m == 1 || m == 2 || m == 3 || m == 5 || m == 6 || m == 7 || m == 9, "twiddle index");
+    C w; w.x = real_const<R>(cr); w.y = real_const<R>(ci);
+    return cmul(v, w);
   }
-  if (INV) ci = -ci;
-  C w; w.x = R(cr); w.y = R(ci);
-  return cmul(v, w);
 }
 
 template <bool INV, typename C>
@@ -157,7 +163,7 @@ AAO_HD void dft_r(C* v) {
 // them (in the padded layout the offsets hold because no element of a group crosses
 // a 16-element padding boundary relative to its base: see the static_assert).
 template <int L, int NS, int NT, int RX, bool INV, int LAY, int LS, typename C>
-__device__ __forceinline__ void fft_stage_r(C* buf, const C* tw) {
+__device__ __forceinline__ void fft_stage_body(C* buf, const C* tw) {
   using Y = SLay<L, NS, LAY>;
   constexpr int Q = L / RX;
   constexpr int TASKS = NS * Q;
@@ -191,6 +197,24 @@ __device__ __forceinline__ void fft_stage_r(C* buf, const C* tw) {
     for (int r = 0; r < RX; ++r) o[Y::off(r * LS)] = v[t][r];
   }
   __syncthreads();
+}
+
+// Double-float stages are called rather than inlined: one radix-16 stage in
+// double-word arithmetic is several thousand instructions, and inlining the four
+// transforms of the time pipeline (and both passes of a DST) would overflow the
+// instruction cache.  The call passes two pointers; everything else stays in the stage.
+template <typename C> struct StageCalled { static constexpr bool value = false; };
+template <> struct StageCalled<dfl2> { static constexpr bool value = true; };
+
+template <int L, int NS, int NT, int RX, bool INV, int LAY, int LS, typename C>
+__device__ __noinline__ void fft_stage_call(C* buf, const C* tw) {
+  fft_stage_body<L, NS, NT, RX, INV, LAY, LS>(buf, tw);
+}
+
+template <int L, int NS, int NT, int RX, bool INV, int LAY, int LS, typename C>
+__device__ __forceinline__ void fft_stage_r(C* buf, const C* tw) {
+  if constexpr (StageCalled<C>::value) fft_stage_call<L, NS, NT, RX, INV, LAY, LS>(buf, tw);
+  else fft_stage_body<L, NS, NT, RX, INV, LAY, LS>(buf, tw);
 }
 
 // Radix-4 stage plan from span LS on, with one radix-2 stage last when log2(L) is odd.

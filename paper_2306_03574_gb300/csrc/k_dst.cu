@@ -14,10 +14,20 @@
 // The factor sqrt(2/M) and the 1/2 of the separation are folded into the
 // pre-processing weights.  The odd outputs are a prefix sum over k, done per
 // thread block of k and then across the threads of a line pair by shuffles.
+//
+// R is the arithmetic type (double, float or the double-float dfl), TIO the type of
+// the vectors in memory (R itself, or double for the double-float kernels).
 #include "aao_internal.cuh"
+#include "dfloat.cuh"
 #include "fft_smem.cuh"
 
 namespace aao {
+
+__device__ __forceinline__ double shfl_up(double v, int off, int w) { return __shfl_up_sync(0xffffffffu, v, off, w); }
+__device__ __forceinline__ float shfl_up(float v, int off, int w) { return __shfl_up_sync(0xffffffffu, v, off, w); }
+__device__ __forceinline__ dfl shfl_up(dfl v, int off, int w) {
+  return dfl(__shfl_up_sync(0xffffffffu, v.hi, off, w), __shfl_up_sync(0xffffffffu, v.lo, off, w));
+}
 
 struct DstArgs {
   int N;            // line length
@@ -26,8 +36,8 @@ struct DstArgs {
   long long nouter; // strided axis: number of outer blocks
 };
 
-template <typename R, int M, int NS, int NT, bool STRIDED, int FFTV>
-__global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, PrecTables<R> tb) {
+template <typename R, typename TIO, int M, int NS, int NT, bool STRIDED, int FFTV>
+__global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
   constexpr int H = M / 2;
   constexpr int TPS = NT / NS;     // threads per line pair in the post-processing
@@ -60,41 +70,41 @@ __global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, Prec
     int q, j;
     if (!STRIDED) { q = task / H; j = task % H + 1; }
     else { q = task % NS; j = task / NS + 1; }
-    R xa0 = 0, xa1 = 0, xb0 = 0, xb1 = 0;  // x_j, x_{M-j} of lines a, b
+    R xa0 = R(), xa1 = R(), xb0 = R(), xb1 = R();  // x_j, x_{M-j} of lines a, b
     if (!STRIDED) {
       const long long la = line0 + 2 * q;
       if (la < a.nlines) {
-        const R* p = in + la * N;
-        xa0 = p[j - 1];
-        xa1 = p[M - j - 1];
+        const TIO* p = in + la * N;
+        xa0 = R(p[j - 1]);
+        xa1 = R(p[M - j - 1]);
       }
       if (la + 1 < a.nlines) {
-        const R* p = in + (la + 1) * N;
-        xb0 = p[j - 1];
-        xb1 = p[M - j - 1];
+        const TIO* p = in + (la + 1) * N;
+        xb0 = R(p[j - 1]);
+        xb1 = R(p[M - j - 1]);
       }
     } else {
       const int ia = i0 + 2 * q;
-      const R* p = in + obase + ia;
+      const TIO* p = in + obase + ia;
       if (ia < a.st) {
-        xa0 = p[(long long)(j - 1) * a.st];
-        xa1 = p[(long long)(M - j - 1) * a.st];
+        xa0 = R(p[(long long)(j - 1) * a.st]);
+        xa1 = R(p[(long long)(M - j - 1) * a.st]);
       }
       if (ia + 1 < a.st) {
-        xb0 = p[(long long)(j - 1) * a.st + 1];
-        xb1 = p[(long long)(M - j - 1) * a.st + 1];
+        xb0 = R(p[(long long)(j - 1) * a.st + 1]);
+        xb1 = R(p[(long long)(M - j - 1) * a.st + 1]);
       }
     }
     const R w = sw[j];
     const R sa = xa0 + xa1, ta = cq * (xa0 - xa1);
     const R sb = xb0 + xb1, tbb = cq * (xb0 - xb1);
     C lo, hi;
-    lo.x = fma(w, sa, ta);  lo.y = fma(w, sb, tbb);
-    hi.x = fma(w, sa, -ta); hi.y = fma(w, sb, -tbb);
+    lo.x = fmadd(w, sa, ta);  lo.y = fmadd(w, sb, tbb);
+    hi.x = fmadd(w, sa, -ta); hi.y = fmadd(w, sb, -tbb);
     cbuf[q * M + j] = lo;
     if (j != H) cbuf[q * M + M - j] = hi;
   }
-  for (int q = tid; q < NS; q += NT) { C z; z.x = 0; z.y = 0; cbuf[q * M] = z; }
+  for (int q = tid; q < NS; q += NT) { C z; z.x = R(); z.y = R(); cbuf[q * M] = z; }
   __syncthreads();
 
   if constexpr (FFTV == 0) fft_block<M, NS, NT, false>(cbuf, tw);
@@ -105,14 +115,14 @@ __global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, Prec
   const int k0 = lq * KQ;
   R pa[KQ], pb[KQ], ia[KQ], ib[KQ];
   {
-    R acc_a = 0, acc_b = 0;
+    R acc_a = R(), acc_b = R();
 #pragma unroll
     for (int i = 0; i < KQ; ++i) {
       const int k = k0 + i;
       const C ck = cbuf[q * M + k];
       R ra, rb;
       if (k == 0) {
-        ra = ck.x; rb = ck.y; ia[i] = 0; ib[i] = 0;
+        ra = ck.x; rb = ck.y; ia[i] = R(); ib[i] = R();
       } else {
         const C cm = cbuf[q * M + M - k];
         ra = ck.x + cm.x; rb = ck.y + cm.y;
@@ -126,13 +136,13 @@ __global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, Prec
   R inc_a = pa[KQ - 1], inc_b = pb[KQ - 1];
 #pragma unroll
   for (int off = 1; off < TPS; off <<= 1) {
-    const R ua = __shfl_up_sync(0xffffffffu, inc_a, off, TPS);
-    const R ub = __shfl_up_sync(0xffffffffu, inc_b, off, TPS);
+    const R ua = shfl_up(inc_a, off, TPS);
+    const R ub = shfl_up(inc_b, off, TPS);
     if (lq >= off) { inc_a += ua; inc_b += ub; }
   }
-  R ex_a = __shfl_up_sync(0xffffffffu, inc_a, 1, TPS);
-  R ex_b = __shfl_up_sync(0xffffffffu, inc_b, 1, TPS);
-  if (lq == 0) { ex_a = 0; ex_b = 0; }
+  R ex_a = shfl_up(inc_a, 1, TPS);
+  R ex_b = shfl_up(inc_b, 1, TPS);
+  if (lq == 0) { ex_a = R(); ex_b = R(); }
   __syncthreads();  // all reads of the spectrum are done
 #pragma unroll
   for (int i = 0; i < KQ; ++i) {
@@ -148,13 +158,16 @@ __global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, Prec
 
   // ---- store ----
   if (!STRIDED) {
+    // line by line (no division by the runtime length N); rows are contiguous in memory
     const long long e0 = line0 * N;
-    const long long etot = a.nlines * (long long)N;
-    for (int e = tid; e < 2 * NS * N; e += NT) {
-      if (e0 + e >= etot) break;
-      const int l = e / N, j = e % N;
-      const C v = cbuf[(l >> 1) * M + j];
-      out[e0 + e] = (l & 1) ? v.y : v.x;
+    for (int l = 0; l < 2 * NS; ++l) {
+      if (line0 + l >= a.nlines) break;
+      const C* row = cbuf + (l >> 1) * M;
+      TIO* o = out + e0 + (long long)l * N;
+      for (int j = tid; j < N; j += NT) {
+        const C v = row[j];
+        o[j] = TIO((l & 1) ? v.y : v.x);
+      }
     }
   } else {
     for (int task = tid; task < 2 * NS * N; task += NT) {
@@ -162,14 +175,14 @@ __global__ void __launch_bounds__(NT) k_dst(const R* in, R* out, DstArgs a, Prec
       const int il = i0 + l;
       if (il < a.st) {
         const C v = cbuf[(l >> 1) * M + j];
-        out[obase + (long long)j * a.st + il] = (l & 1) ? v.y : v.x;
+        out[obase + (long long)j * a.st + il] = TIO((l & 1) ? v.y : v.x);
       }
     }
   }
 }
 
-template <typename R, int M, int FFTV>
-static cudaError_t dst_launch_MV(const Plan& P, const R* in, R* out, int axis, int nrhs,
+template <typename R, typename TIO, int M, int FFTV>
+static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs,
                                  cudaStream_t s) {
   using C = typename Cplx<R>::T;
   constexpr int NT = 128;
@@ -185,7 +198,7 @@ static cudaError_t dst_launch_MV(const Plan& P, const R* in, R* out, int axis, i
     a.nlines = total / P.N;
     a.st = 1;
     a.nouter = 0;
-    auto kern = k_dst<R, M, NS, NT, false, FFTV>;
+    auto kern = k_dst<R, TIO, M, NS, NT, false, FFTV>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const long long nb = (a.nlines + 2 * NS - 1) / (2 * NS);
     kern<<<dim3((unsigned)nb), NT, smem, s>>>(in, out, a, tb);
@@ -193,7 +206,7 @@ static cudaError_t dst_launch_MV(const Plan& P, const R* in, R* out, int axis, i
     a.st = (int)stride;
     a.nouter = total / (stride * P.N);
     a.nlines = 0;
-    auto kern = k_dst<R, M, NS, NT, true, FFTV>;
+    auto kern = k_dst<R, TIO, M, NS, NT, true, FFTV>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int ntile = (int)((stride + 2 * NS - 1) / (2 * NS));
     kern<<<dim3((unsigned)a.nouter, (unsigned)ntile), NT, smem, s>>>(in, out, a, tb);
@@ -201,24 +214,35 @@ static cudaError_t dst_launch_MV(const Plan& P, const R* in, R* out, int axis, i
   return cudaGetLastError();
 }
 
-template <typename R, int M>
-static cudaError_t dst_launch_M(const Plan& P, const R* in, R* out, int axis, int nrhs,
+template <typename R, typename TIO, int M>
+static cudaError_t dst_launch_M(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs,
                                 cudaStream_t s) {
-  return P.dst_variant ? dst_launch_MV<R, M, 1>(P, in, out, axis, nrhs, s)
-                       : dst_launch_MV<R, M, 0>(P, in, out, axis, nrhs, s);
+  return P.dst_variant ? dst_launch_MV<R, TIO, M, 1>(P, in, out, axis, nrhs, s)
+                       : dst_launch_MV<R, TIO, M, 0>(P, in, out, axis, nrhs, s);
+}
+
+template <typename R, typename TIO>
+static cudaError_t dst_dispatch(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs, cudaStream_t s) {
+  switch (P.M) {
+    case 64: return dst_launch_M<R, TIO, 64>(P, in, out, axis, nrhs, s);
+    case 128: return dst_launch_M<R, TIO, 128>(P, in, out, axis, nrhs, s);
+    case 256: return dst_launch_M<R, TIO, 256>(P, in, out, axis, nrhs, s);
+    case 512: return dst_launch_M<R, TIO, 512>(P, in, out, axis, nrhs, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename R>
 cudaError_t launch_dst_axis(const Plan& P, const R* in, R* out, int axis, int nrhs,
                             cudaStream_t s, uint64_t* nl) {
   if (nl) ++*nl;
-  switch (P.M) {
-    case 64: return dst_launch_M<R, 64>(P, in, out, axis, nrhs, s);
-    case 128: return dst_launch_M<R, 128>(P, in, out, axis, nrhs, s);
-    case 256: return dst_launch_M<R, 256>(P, in, out, axis, nrhs, s);
-    case 512: return dst_launch_M<R, 512>(P, in, out, axis, nrhs, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return dst_dispatch<R, R>(P, in, out, axis, nrhs, s);
+}
+
+cudaError_t launch_dst_axis_ff(const Plan& P, const double* in, double* out, int axis, int nrhs,
+                               cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  return dst_dispatch<dfl, double>(P, in, out, axis, nrhs, s);
 }
 
 template cudaError_t launch_dst_axis<double>(const Plan&, const double*, double*, int, int,

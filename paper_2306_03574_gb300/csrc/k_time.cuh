@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
     const TIO* p = in + rb + (long long)t * m + sa;
     const R di = dinv[t];
     C z;
-    z.x = (sa < m) ? R(p[0]) * di : R(0);
-    z.y = (sa + 1 < m) ? R(p[1]) * di : R(0);
+    z.x = (sa < m) ? R(p[0]) * di : R();
+    z.y = (sa + 1 < m) ? R(p[1]) * di : R();
     cbuf[Y::at(q, t)] = z;
   }
   if constexpr (STAGED) cp_async_wait_all();

@@ -1,5 +1,6 @@
-"""Double-float mode (AAO_PREC_F32X2): the time part of P_alpha^{-1} in pairs of FP32
-numbers on the FP32 pipes, everything else FP64.  Parity of the time pipeline and of
+"""Double-float mode (AAO_PREC_F32X2): P_alpha^{-1} and the DSTs of the solve in pairs
+of FP32 numbers on the FP32 pipes, operator and recurrences FP64.  Parity of the DST,
+the time pipeline and
 P_alpha^{-1} against the FP64 oracle within the error the alpha-scaling implies for
 ~47-bit arithmetic, every kernel variant, and solves that reach the FP64 true
 relative residual 1e-8 checked with the oracle operator."""
@@ -104,7 +105,7 @@ def test_f32x2_solve_reaches_fp64_tolerance(N, nt):
 
 def test_f32x2_batched_and_variable_coefficient():
     """Batched right-hand sides give the single results; the variable-coefficient path
-    (physical basis, the full P^{-1} with FP64 DSTs and the double-float time part)
+    (physical basis, the full double-float P^{-1} every iteration)
     reaches 1e-8."""
     p = W.config_2d(N=63, nt=64, alpha=1e-6)
     f2 = np.stack([p.f, 2.0 * p.f + 1e-3])
@@ -136,3 +137,44 @@ def test_f32x2_batched_and_variable_coefficient():
     bo = OS.rhs_b_var(q, faces)
     rel = np.linalg.norm(bo - OS.apply_YT_var(xs, faces, 2, 63, q.tau)) / np.linalg.norm(bo)
     assert rel <= 1e-8 * 1.01
+
+
+@pytest.mark.parametrize("d,N", [(1, 511), (2, 63), (2, 255), (3, 63)])
+def test_f32x2_dst_parity(d, N, monkeypatch):
+    """The double-float DST-I (both stage plans, every axis) against the oracle's explicit
+    DST matrices: ~47-bit accuracy, far below FP32 and near FP64."""
+    nt = 64
+    x = W.random_field((nt, N ** d), seed=2500 + N + d)
+    ref = OF.apply_space(x, OF.dst_matrix(N), d, N)
+    for dv in range(2):
+        monkeypatch.setenv("AAO_DST_VARIANT", str(dv))
+        with aao.Solver(d, N, nt, 1.0 / nt, 0.1, precision=aao.AAO_PREC_F32X2) as s:
+            xt = cu(x)
+            yt = torch.empty_like(xt)
+            s.apply_dst(xt, yt)
+            torch.cuda.synchronize()
+            assert relerr(yt.cpu().numpy(), ref) < 64 * U_DW * np.log2(N + 1) * d, dv
+
+
+@pytest.mark.parametrize("scale", [1e-25, 1e-3, 1.0, 1e30])
+def test_f32x2_conversions_across_scales(scale):
+    """The double <-> double-float conversions in the loads and stores take a fast path
+    (bit fields, exponents in [-70, 120]) and a fallback (other exponents): scaled
+    inputs that land in each give the same relative accuracy, zeros stay zeros, and
+    exactly representable inputs survive the round trip."""
+    d, N, nt = 2, 63, 64
+    x = W.random_field((nt, N ** d), seed=2600) * scale
+    x[5] = 0.0                      # a whole time level of zeros
+    ref = OF.apply_space(x, OF.dst_matrix(N), d, N)
+    with aao.Solver(d, N, nt, 1.0 / nt, 0.1, precision=aao.AAO_PREC_F32X2) as s:
+        xt = cu(x)
+        yt = torch.empty_like(xt)
+        s.apply_dst(xt, yt)
+        torch.cuda.synchronize()
+        y = yt.cpu().numpy()
+        assert relerr(y, ref) < 64 * U_DW * np.log2(N + 1) * d
+        assert np.all(y[5] == 0.0)
+        # U is an involution: applying it again returns x to the same accuracy
+        s.apply_dst(yt, yt)
+        torch.cuda.synchronize()
+        assert relerr(yt.cpu().numpy(), x) < 2 * 64 * U_DW * np.log2(N + 1) * d
