@@ -67,7 +67,8 @@ typedef enum aao_scheme { AAO_SCHEME_IMPLICIT_LEAPFROG = 0 } aao_scheme;
 typedef enum aao_precision {
   AAO_PREC_FP64 = 0,     /* everything in FP64 */
   AAO_PREC_FP32_IR = 1,  /* P_alpha^{-1} in FP32/complex64; operator, MINRES recurrences,
-                            residuals and an outer iterative refinement in FP64 */
+                            residuals and an outer iterative refinement in FP64; the DSTs
+                            of b and x (and aao_apply_dst) in double-float (see below) */
   AAO_PREC_F32X2 = 2     /* P_alpha^{-1} (DSTs and time part) and the DSTs of the solve in
                             double-float arithmetic (pairs of FP32 numbers, ~47 significant
                             bits, on the FP32 pipes) on FP64 vectors; operator, recurrences and
@@ -168,7 +169,8 @@ aao_status aao_apply_prec(aao_handle* h, const double* r, double* z, int nrhs, v
  * DST-I (Section 2.3: on a uniform grid the eigenvector matrix U of L is the
  * DST); U = U^T = U^{-1}.  This is the spatial part of P_alpha^{-1}, exposed on
  * its own.  x, y: nrhs x n x m FP64 vectors, may be equal; FP64 arithmetic, or
- * double-float for an AAO_PREC_F32X2 handle.  Errors: AAO_EINVAL, AAO_ECUDA. */
+ * double-float for AAO_PREC_F32X2 and AAO_PREC_FP32_IR handles.  Errors: AAO_EINVAL,
+ * AAO_ECUDA. */
 aao_status aao_apply_dst(aao_handle* h, const double* x, double* y, int nrhs, void* stream);
 
 /* The time part of P_alpha^{-1} on DST coefficients: for every spatial mode j

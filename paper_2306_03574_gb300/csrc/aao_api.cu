@@ -285,10 +285,12 @@ aao_status time_apply(aao_handle* h, const double* in, double* out, int nrhs, cu
   return AAO_OK;
 }
 
-// (I (x) U) in -> out (FP64 vectors; out may equal in); double-float arithmetic for an
-// AAO_PREC_F32X2 handle, FP64 otherwise
+// (I (x) U) in -> out (FP64 vectors; out may equal in); double-float arithmetic for the
+// AAO_PREC_F32X2 and AAO_PREC_FP32_IR handles (the refinement's b^ and x need ~1e-14
+// relative accuracy, which double-float gives at two thirds of the FP64 cost), FP64
+// otherwise
 aao_status dst_apply(aao_handle* h, const double* in, double* out, int nrhs, cudaStream_t s) {
-  if (h->precision == AAO_PREC_F32X2) {
+  if (h->precision == AAO_PREC_F32X2 || h->precision == AAO_PREC_FP32_IR) {
     AAO_KL(h, KC_DST_XFF, s, launch_dst_axis_ff(h->P, in, out, 0, nrhs, s, &h->launches));
     for (int ax = 1; ax < h->P.d; ++ax)
       AAO_KL(h, KC_DST_XFF + ax, s, launch_dst_axis_ff(h->P, out, out, ax, nrhs, s, &h->launches));
@@ -936,9 +938,12 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     return bail(st);
   const bool fp32 = (o.precision == AAO_PREC_FP32_IR);
   const bool ff = (o.precision == AAO_PREC_F32X2);
+  const bool ff_dst = ff || fp32;  // double-float DSTs (see dst_apply)
+  if (ff_dst) {
+    if ((st = h->alloc(&h->tw_space_ff, M)) || (st = h->alloc(&h->sinw_ff, M / 2 + 1))) return bail(st);
+  }
   if (ff) {
-    if ((st = h->alloc(&h->tw_space_ff, M)) || (st = h->alloc(&h->sinw_ff, M / 2 + 1)) ||
-        (st = h->alloc(&h->tw_time_ff, nt)) || (st = h->alloc(&h->dinv_ff, nt)) ||
+    if ((st = h->alloc(&h->tw_time_ff, nt)) || (st = h->alloc(&h->dinv_ff, nt)) ||
         (st = h->alloc(&h->d2_ff, nt)) || (st = h->alloc(&h->ab_ff, tabn)))
       return bail(st);
   }
@@ -1004,13 +1009,15 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
       P.t32.dinv = h->dinv32; P.t32.d2 = h->d232; P.t32.ab = h->ab32;
       P.t32.cq = (float)(cM / 4.0L);
     }
-    if (ff) {
-      AAO_TRY(upload(to_df2(twT), h->tw_time_ff));
+    if (ff_dst) {
       AAO_TRY(upload(to_df2(twS), h->tw_space_ff));
       AAO_TRY(upload(to_df(sinw), h->sinw_ff));
-      P.tff.tw_time = h->tw_time_ff; P.tff.dinv = h->dinv_ff; P.tff.d2 = h->d2_ff; P.tff.ab = h->ab_ff;
       P.tff.tw_space = h->tw_space_ff; P.tff.sinw = h->sinw_ff;
       P.tff.cq = dfl((double)(cM / 4.0L));
+    }
+    if (ff) {
+      AAO_TRY(upload(to_df2(twT), h->tw_time_ff));
+      P.tff.tw_time = h->tw_time_ff; P.tff.dinv = h->dinv_ff; P.tff.d2 = h->d2_ff; P.tff.ab = h->ab_ff;
     }
     AAO_TRY(set_params(h, tau, alpha, grid->c2, 0));
     AAO_CK(cudaDeviceSynchronize());
