@@ -204,7 +204,7 @@ def traffic_record(cls: str, variant=None):
         return None
     if variant is not None and r.get("variant") is not None and r["variant"] != variant:
         return None
-    if r.get("workload") != WORKLOAD_NAME[0]:
+    if WORKLOAD_NAME[0] not in r.get("workloads", [r.get("workload")]):
         return None
     return r.get("bytes_per_launch")
 

@@ -311,7 +311,9 @@ const char* aao_serve_last_error(void);
  * 2048/n mode pairs per CTA; shared-memory layout: sequence-major or interleaved and
  * padded) and of the DST kernel (radix-4 or radix-16 stage plan) by
  * timing each on the handle's workspace with CUDA events (the work of the kernels is
- * the same in every variant; only speed differs).  tune_file (host string, may be
+ * the same in every variant; only speed differs).  The default variant is kept unless
+ * another is more than 1 % faster, so near-ties give the same choice on every run.
+ * tune_file (host string, may be
  * NULL): a text file of cached choices, one line "dim N nt precision time dst"; a
  * matching line is applied without measuring, otherwise the measured choice is
  * appended.  chosen (host, may be NULL): receives {time variant, DST variant}.

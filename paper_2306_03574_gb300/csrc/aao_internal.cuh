@@ -113,6 +113,10 @@ cudaError_t launch_split_df(const double2* in, dfl2* out, size_t count, cudaStre
 
 cudaError_t launch_build_rhs(const Plan& P, const double* f, const double* psi0, const double* psi1,
                              double* b, int nrhs, cudaStream_t s, uint64_t* nl);
+// The same for one right-hand side (f, psi0, psi1, b point at it) and the f levels
+// k0 .. k0+cnt-1 only (they fill the b levels n-1-k0-cnt+1 .. n-1-k0).
+cudaError_t launch_build_rhs_levels(const Plan& P, const double* f, const double* psi0, const double* psi1,
+                                    double* b, int k0, int cnt, cudaStream_t s, uint64_t* nl);
 // Variable coefficient (face arrays, see aao_set_coefficient): operator and right-hand side.
 cudaError_t launch_yt_var(const Plan& P, const double* face, const double* x, double* y, const double* w,
                           double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);

@@ -245,13 +245,14 @@ __global__ void __launch_bounds__(YT_NT) k_rhs_var(const double* __restrict__ f,
 }
 
 // b[n-1-k] = tau^2 f^k for k >= 2; tau^2 f^1 - L psi0; tau^2 f^0/2 + tau psi1 + psi0.
+// (levels k0 .. k0 + gridDim.y - 1 of every right-hand side)
 template <int D>
 __global__ void __launch_bounds__(YT_NT) k_rhs(const double* __restrict__ f,
                                                const double* __restrict__ psi0,
                                                const double* __restrict__ psi1,
-                                               double* __restrict__ b, YtArgs a, double tau) {
+                                               double* __restrict__ b, YtArgs a, double tau, int k0) {
   const int s = blockIdx.x * YT_NT + threadIdx.x;
-  const int k = blockIdx.y;
+  const int k = k0 + blockIdx.y;
   const int n = a.n, m = a.m, N = a.N;
   if (s >= m) return;
   const long long rb = (long long)blockIdx.z * n * m;
@@ -377,9 +378,24 @@ cudaError_t launch_build_rhs(const Plan& P, const double* f, const double* psi0,
   const YtArgs a = make_args(P);
   dim3 g((P.m + YT_NT - 1) / YT_NT, P.n, nrhs);
   switch (P.d) {
-    case 1: k_rhs<1><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
-    case 2: k_rhs<2><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
-    case 3: k_rhs<3><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau); break;
+    case 1: k_rhs<1><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau, 0); break;
+    case 2: k_rhs<2><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau, 0); break;
+    case 3: k_rhs<3><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau, 0); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_rhs_levels(const Plan& P, const double* f, const double* psi0, const double* psi1,
+                                    double* b, int k0, int cnt, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  if (k0 < 0 || cnt < 1 || k0 + cnt > P.n) return cudaErrorInvalidValue;
+  const YtArgs a = make_args(P);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, cnt, 1);
+  switch (P.d) {
+    case 1: k_rhs<1><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau, k0); break;
+    case 2: k_rhs<2><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau, k0); break;
+    case 3: k_rhs<3><<<g, YT_NT, 0, s>>>(f, psi0, psi1, b, a, P.tau, k0); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -96,3 +96,31 @@ def test_autotune_keeps_results_and_caches(tmp_path):
             assert np.abs(zt.cpu().numpy() - ref).max() / np.abs(ref).max() < 1e-12
     lines = open(tf).read().strip().splitlines()
     assert len(lines) == 1 and lines[0].split()[:4] == ["2", "127", "128", "0"]
+
+
+@pytest.mark.parametrize("prec", [aao.AAO_PREC_FP64, aao.AAO_PREC_F32X2, aao.AAO_PREC_FP32_IR])
+@pytest.mark.parametrize("graph", [True, False])
+def test_host_buffer_solve_equals_device_solve(prec, graph):
+    """aao_solve_host pipelines its copies with the right-hand side, the DSTs and the
+    solve in chunks of time levels; the result is bit for bit the device-buffer solve of
+    the same data (two right-hand sides, pinned and pageable host memory)."""
+    p = W.config_2d(N=63, nt=128, alpha=1e-3 if prec == aao.AAO_PREC_FP32_IR else 1e-6)
+    f2 = np.stack([p.f, 0.5 * p.f + 1e-3])
+    p0 = np.stack([p.psi0, -p.psi0])
+    p1 = np.stack([p.psi1, p.psi1 + 0.1])
+    with aao.Solver(2, p.N, p.nt, p.tau, p.alpha, precision=prec, nrhs_max=2, graph=graph) as s:
+        b = torch.empty((2, p.nt, p.m), dtype=torch.float64, device="cuda")
+        s.build_rhs(cu(f2), cu(p0), cu(p1), b)
+        x = torch.empty_like(b)
+        st, info = s.solve(b, x, rtol=1e-9, maxit=100)
+        assert st == aao.AAO_OK
+        ref = x.cpu().numpy()
+        for pinned in (True, False):
+            fh = torch.from_numpy(f2.copy())
+            uh = torch.empty((2, p.nt, p.m), dtype=torch.float64)
+            if pinned:
+                fh, uh = fh.pin_memory(), uh.pin_memory()
+            st, info2 = s.solve_host(fh, p0.copy(), p1.copy(), uh, rtol=1e-9, maxit=100)
+            assert st == aao.AAO_OK
+            assert np.array_equal(uh.numpy(), ref), pinned
+            assert [i["iters"] for i in info2] == [i["iters"] for i in info]
