@@ -727,6 +727,7 @@ def run_served(args, world, rank, local):
     dev = torch.device("cuda", local)
     count = args.requests
     rate = float(args.rate)
+    sprec = aao.AAO_PREC_F32X2 if args.serve_precision == "f32x2" else aao.AAO_PREC_FP64
     reqs = W.served_requests(count=count, rate=rate, seed=5 + rank)
     # per-shape device data (source, initial values) shared by the requests of that shape;
     # wave speed, tolerance and the output buffer differ per request
@@ -749,7 +750,7 @@ def run_served(args, world, rank, local):
         key = (r["d"], r["N"], r["nt"])
         sh = shapes[key]
         return aao.aao_serve_submit(srv, r["d"], r["N"], r["nt"], sh["tau"], 1e-6, r["c2"], r["tol"], 100,
-                                    sh["f"], sh["psi0"], sh["psi1"], x)
+                                    sh["f"], sh["psi0"], sh["psi1"], x, precision=sprec)
 
     # warm-up: one request per shape (handles, tables, captured graphs), untimed
     for key in shapes:
@@ -797,7 +798,7 @@ def run_served(args, world, rank, local):
     for rid, (rr, xs) in sample.items():
         key = (rr["d"], rr["N"], rr["nt"])
         sh = shapes[key]
-        with aao.Solver(rr["d"], rr["N"], rr["nt"], sh["tau"], 1e-6, c2=rr["c2"], graph=True) as s1:
+        with aao.Solver(rr["d"], rr["N"], rr["nt"], sh["tau"], 1e-6, c2=rr["c2"], graph=True, precision=sprec) as s1:
             b = torch.empty((rr["nt"], sh["m"]), dtype=torch.float64, device=dev)
             s1.build_rhs(sh["f"], sh["psi0"], sh["psi1"], b)
             x1 = torch.empty_like(b)
@@ -809,8 +810,10 @@ def run_served(args, world, rank, local):
         "metric": f"served solves/s with p50/p99 latency (Poisson {rate:g}/s, mixed 1D/2D, 120 GB budget)",
         "value": len(ok) / (t_last - t_first), "unit": "solves/s", "n_gpus": world,
         "steps": len(reqs), "warmup": len(shapes), "ms_per_step": 1e3 * (t_last - t_first) / max(len(ok), 1),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"served_poisson{rate:g}_mixed_1d2d_fp64", "requests": len(reqs), "slots": args.slots,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.serve_precision == "fp64" else "f32x2+f64", "data": "synthetic",
+        "config": {"workload": f"served_poisson{rate:g}_mixed_1d2d_{args.serve_precision}", "requests": len(reqs),
+                   "slots": args.slots,
                    "budget_bytes": int(120e9), "shapes": len(shapes)},
         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                        "mean": float(lat.mean() * 1e3), "max": float(lat.max() * 1e3)},
@@ -834,6 +837,8 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="served workload: concurrent solves")
     ap.add_argument("--rate", type=float, default=200.0, help="served workload: mean Poisson arrival rate (1/s)")
+    ap.add_argument("--serve-precision", choices=["fp64", "f32x2"], default="fp64",
+                    help="served workload: precision mode of every request")
     ap.add_argument("--alpha", type=float, default=None)
     ap.add_argument("--graph", type=int, default=1,
                     help="1: solve loop captured in a CUDA graph (device-side while loop); 0: host-driven")

@@ -261,6 +261,8 @@ typedef struct aao_request {
   const double* psi0;    /* device, m */
   const double* psi1;    /* device, m */
   double* x;             /* device, n x m solution output (written by the server) */
+  int precision;         /* AAO_PREC_FP64 (0, the default of a zeroed request) or
+                            AAO_PREC_F32X2; the refinement mode is not served */
 } aao_request;
 
 typedef struct aao_serve_result {

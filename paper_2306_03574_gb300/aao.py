@@ -65,7 +65,7 @@ class aao_request(ctypes.Structure):
                 ("tau", ctypes.c_double), ("alpha", ctypes.c_double), ("c2", ctypes.c_double),
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("f", ctypes.c_void_p), ("psi0", ctypes.c_void_p), ("psi1", ctypes.c_void_p),
-                ("x", ctypes.c_void_p)]
+                ("x", ctypes.c_void_p), ("precision", ctypes.c_int)]
 
 
 class aao_serve_result(ctypes.Structure):
@@ -323,9 +323,10 @@ def aao_serve_create(hbm_budget_bytes: int, max_slots: int, raw_status: bool = F
     return s.value
 
 
-def aao_serve_submit(srv, dim, N, nt, tau, alpha, c2, rtol, maxit, f, psi0, psi1, x) -> int:
+def aao_serve_submit(srv, dim, N, nt, tau, alpha, c2, rtol, maxit, f, psi0, psi1, x,
+                     precision: int = AAO_PREC_FP64) -> int:
     r = aao_request(dim, N, nt, tau, alpha, c2, rtol, maxit, _dev_ptr(f), _dev_ptr(psi0), _dev_ptr(psi1),
-                    _dev_ptr(x))
+                    _dev_ptr(x), precision)
     t = ctypes.c_uint64()
     st = lib().aao_serve_submit(srv, ctypes.byref(r), ctypes.byref(t))
     if st != AAO_OK:

@@ -813,8 +813,8 @@ aao_status aaoi_rebind(aao_handle* h, double tau, double alpha, double c2) {
 aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double rtol, int maxit,
                               cudaStream_t s) {
   if (!h || !b || !x) return fail(AAO_EINVAL, "null pointer");
-  if (h->precision != AAO_PREC_FP64 || h->var_on || !h->use_graph)
-    return fail(AAO_EINVAL, "asynchronous solves need an FP64, constant-coefficient, graph handle");
+  if ((h->precision != AAO_PREC_FP64 && h->precision != AAO_PREC_F32X2) || h->var_on || !h->use_graph)
+    return fail(AAO_EINVAL, "asynchronous solves need an FP64 or double-float, constant-coefficient, graph handle");
   AAO_TRY(dst_apply(h, b, h->vbh, 1, s));
   MinresCtx c{h, h->vbh, h->vxh, 1, rtol, maxit, s, true, false};
   cudaGraphExec_t ex = nullptr;
@@ -842,13 +842,14 @@ aao_status aaoi_solve_collect(aao_handle* h, double rtol, aao_solve_info* info) 
   return st;
 }
 
-size_t aaoi_estimate_bytes(int dim, int N, int nt) {
+size_t aaoi_estimate_bytes(int dim, int N, int nt, int precision) {
   size_t m = 1;
   for (int i = 0; i < dim; ++i) m *= (size_t)N;
   const size_t npairs = (m + 1) / 2;
   const size_t vec = (size_t)nt * m * sizeof(double);
   const size_t nbyt = ((m + 255) / 256) * (((size_t)nt + 31) / 32);
-  return 9 * vec + (size_t)(nt / 2 + 1) * npairs * 2 * sizeof(double2) + m * sizeof(double) +
+  const size_t table = (size_t)(nt / 2 + 1) * npairs * 2 * sizeof(double2);  // FP64 (and dfl2) table
+  return 9 * vec + (precision == AAO_PREC_F32X2 ? 2 : 1) * table + m * sizeof(double) +
          3 * std::max(nbyt, (size_t)296) * sizeof(double) + (1 << 16);
 }
 

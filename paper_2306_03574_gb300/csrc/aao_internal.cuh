@@ -176,4 +176,4 @@ aao_status aaoi_rebind(aao_handle* h, double tau, double alpha, double c2);
 aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double rtol, int maxit,
                               cudaStream_t s);
 aao_status aaoi_solve_collect(aao_handle* h, double rtol, aao_solve_info* info);
-size_t aaoi_estimate_bytes(int dim, int N, int nt);
+size_t aaoi_estimate_bytes(int dim, int N, int nt, int precision);

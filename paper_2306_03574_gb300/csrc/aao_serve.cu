@@ -33,7 +33,7 @@ using Clock = std::chrono::steady_clock;
 struct PoolEntry {
   aao_handle* h = nullptr;
   double* b = nullptr;  // right-hand side built by the server for this handle's requests
-  int dim = 0, N = 0, nt = 0;
+  int dim = 0, N = 0, nt = 0, precision = 0;
   size_t bytes = 0;
   bool busy = false;
   uint64_t last_used = 0;
@@ -120,8 +120,9 @@ struct aao_server {
   PoolEntry* acquire(const aao_request& q, aao_status* err) {
     *err = AAO_OK;
     for (PoolEntry* pe : pool)
-      if (!pe->busy && pe->dim == q.dim && pe->N == q.N && pe->nt == q.nt) return pe;
-    const size_t need = aaoi_estimate_bytes(q.dim, q.N, q.nt) + (size_t)q.nt * 8 *
+      if (!pe->busy && pe->dim == q.dim && pe->N == q.N && pe->nt == q.nt && pe->precision == q.precision)
+        return pe;
+    const size_t need = aaoi_estimate_bytes(q.dim, q.N, q.nt, q.precision) + (size_t)q.nt * 8 *
                         (size_t)std::pow((double)q.N, (double)q.dim);
     if (need > budget) {
       *err = AAO_ENOMEM;
@@ -136,7 +137,7 @@ struct aao_server {
     }
     aao_grid g{q.dim, q.N, q.c2};
     aao_opts o{};
-    o.precision = AAO_PREC_FP64;
+    o.precision = q.precision;
     o.nrhs_max = 1;
     o.graph = 1;
     aao_handle* h = nullptr;
@@ -159,6 +160,7 @@ struct aao_server {
     pe->dim = q.dim;
     pe->N = q.N;
     pe->nt = q.nt;
+    pe->precision = q.precision;
     pe->bytes = aao_workspace_bytes(h) + vb;
     pool.push_back(pe);
     pool_bytes += pe->bytes;
@@ -289,6 +291,8 @@ aao_status aao_serve_submit(aao_server* s, const aao_request* r, uint64_t* ticke
     return sfail(AAO_EUNSUPPORTED, "size outside the supported set");
   if (!(r->tau > 0) || !(r->alpha > 0 && r->alpha <= 1) || !(r->c2 > 0) || !(r->rtol >= 0) || r->maxit < 1)
     return sfail(AAO_EINVAL, "bad parameters");
+  if (r->precision != AAO_PREC_FP64 && r->precision != AAO_PREC_F32X2)
+    return sfail(AAO_EINVAL, "served precision must be AAO_PREC_FP64 or AAO_PREC_F32X2");
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) return sfail(AAO_EBUSY, "server is shutting down");
   const uint64_t t = s->next_ticket++;

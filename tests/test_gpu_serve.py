@@ -127,3 +127,39 @@ def test_bounded_wait_times_out_then_completes():
             assert st == aao.AAO_OK
     finally:
         aao.aao_serve_destroy(srv)
+
+
+def test_served_precisions_equal_solo_solves():
+    """Requests may ask for the double-float mode: FP64 and double-float requests of the
+    same shapes get separate pooled handles, and each result equals the same solve run
+    alone in its precision, bit for bit (and meets the FP64 true-residual tolerance)."""
+    reqs = _requests(k=8, seed=91)
+    srv = aao.aao_serve_create(8 << 30, 4)
+    try:
+        tickets = []
+        for i, (r, p, f, p0, p1, x) in enumerate(reqs):
+            prec = aao.AAO_PREC_F32X2 if i % 2 else aao.AAO_PREC_FP64
+            tickets.append((prec, aao.aao_serve_submit(srv, p.d, p.N, p.nt, p.tau, p.alpha, p.c2, r["tol"], 100,
+                                                       f, p0, p1, x, precision=prec)))
+        results = []
+        for prec, t in tickets:
+            st, res = aao.aao_serve_wait(srv, t, 120.0)
+            assert st == aao.AAO_OK, (st, res)
+            results.append(res)
+        with pytest.raises(aao.AaoError):  # the refinement mode is not served
+            r, p, f, p0, p1, x = reqs[0]
+            aao.aao_serve_submit(srv, p.d, p.N, p.nt, p.tau, p.alpha, p.c2, 1e-8, 100, f, p0, p1, x,
+                                 precision=aao.AAO_PREC_FP32_IR)
+    finally:
+        aao.aao_serve_destroy(srv)
+    for (prec, _), (r, p, f, p0, p1, x), res in zip(tickets, reqs, results):
+        with aao.Solver(p.d, p.N, p.nt, p.tau, p.alpha, c2=p.c2, precision=prec, graph=True) as s:
+            b = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
+            s.build_rhs(f, p0, p1, b)
+            xs = torch.empty_like(b)
+            st, info = s.solve(b, xs, rtol=r["tol"], maxit=100)
+            torch.cuda.synchronize()
+        assert st == aao.AAO_OK
+        assert res["iters"] == info[0]["iters"]
+        assert np.array_equal(x.cpu().numpy(), xs.cpu().numpy()), prec
+        assert res["relres_true"] <= r["tol"]
