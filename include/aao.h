@@ -235,7 +235,12 @@ const char* aao_noalloc_last_error(void);
 /* End-to-end solve from HOST buffers: copies f, psi0, psi1 (host, any memory;
  * pinned for speed) to the device, builds b (aao_build_rhs), runs
  * aao_minres_solve from a zero guess, and copies u (host, nrhs x n x m) back.
- * Blocks until u is on the host.  Errors as aao_minres_solve. */
+ * For constant-coefficient FP64 and double-float handles the copies run on a
+ * second stream in chunks of 32 time levels, overlapping the right-hand side and
+ * the DSTs (each level of those depends on its own f level only; the result is
+ * bit for bit the device-buffer solve).  The first call allocates the device
+ * copies of f, b, x and the copy stream.  Blocks until u is on the host.  Errors
+ * as aao_minres_solve, and AAO_ENOMEM. */
 aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, const double* psi1,
                           double* u, int nrhs, double rtol, int maxit,
                           aao_solve_info* info, void* stream);
@@ -245,8 +250,9 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
  * and tolerances onto one GPU under an HBM budget (continuous admission: requests
  * that arrive while others run are started as slots and memory free up; their work
  * runs concurrently on the device).  Not part of the paper: a runtime around its
- * method.  Each request is an FP64 solve of eq. (precsys) as aao_minres_solve does
- * it (zero initial guess, true relative residual <= rtol); the Krylov state stays on
+ * method.  Each request is a solve of eq. (precsys) as aao_minres_solve does it in
+ * the request's precision (FP64 or double-float; zero initial guess, true relative
+ * residual <= rtol); the Krylov state stays on
  * the device for the whole solve (graph-captured loop); a request never shares
  * buffers with another, so its result does not depend on what else is running.
  * --------------------------------------------------------------------------- */
