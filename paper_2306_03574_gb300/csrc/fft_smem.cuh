@@ -148,11 +148,101 @@ AAO_HD void dft16(C* v) {
   }
 }
 
+// Forward 16-point DFT (same 4 x 4 split as dft16) with the internal twiddles folded
+// into fused multiply-adds.  In each column k1 of the second 4-point DFTs the
+// non-trivial twiddles share one real factor: W^2 and W^6 are sqrt(2)/2 times
+// (1 - i) and (-1 - i); W^1, W^3 and W^9 are cos(pi/8) times (1 - i t), (t - i) and
+// (-1 + i t), t = tan(pi/8).  The short factors cost additions or one multiply-add
+// each, and the common factor is applied by the multiply-adds that form the outputs
+// instead of by separate products: 144 real operations instead of 160.
+template <typename C>
+AAO_HD void dft16_fwd_fma(C* v) {
+  using R = decltype(v[0].x);
+  const R h = R(0.70710678118654752440);  // sqrt(2)/2
+  const R c = R(0.92387953251128675613);  // cos(pi/8)
+  const R t = R(0.41421356237309504880);  // tan(pi/8) = sqrt(2) - 1
+  C a[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C x0 = v[n2], x1 = v[4 + n2], x2 = v[8 + n2], x3 = v[12 + n2];
+    dft4<false>(x0, x1, x2, x3);
+    a[4 * n2 + 0] = x0; a[4 * n2 + 1] = x1; a[4 * n2 + 2] = x2; a[4 * n2 + 3] = x3;
+  }
+  {  // k1 = 0: no twiddles
+    C y0 = a[0], y1 = a[4], y2 = a[8], y3 = a[12];
+    dft4<false>(y0, y1, y2, y3);
+    v[0] = y0; v[4] = y1; v[8] = y2; v[12] = y3;
+  }
+  {  // k1 = 2: (a2, a6 W^2, a10 W^4, a14 W^6), a10 W^4 = -i a10, a6 W^2 = h p, a14 W^6 = h r
+    const C b0 = a[2], b2 = a[10], q6 = a[6], q14 = a[14];
+    C e0, e1;
+    e0.x = b0.x + b2.y; e0.y = b0.y - b2.x;
+    e1.x = b0.x - b2.y; e1.y = b0.y + b2.x;
+    const R px = q6.x + q6.y, py = q6.y - q6.x;
+    const R rx = q14.y - q14.x, ry = -q14.x - q14.y;
+    const R sx = px + rx, sy = py + ry, dx = px - rx, dy = py - ry;
+    v[2].x = fmadd(h, sx, e0.x);   v[2].y = fmadd(h, sy, e0.y);     // e0 + h s
+    v[10].x = fmadd(-h, sx, e0.x); v[10].y = fmadd(-h, sy, e0.y);   // e0 - h s
+    v[6].x = fmadd(h, dy, e1.x);   v[6].y = fmadd(-h, dx, e1.y);    // e1 - i h d
+    v[14].x = fmadd(-h, dy, e1.x); v[14].y = fmadd(h, dx, e1.y);    // e1 + i h d
+  }
+  {  // k1 = 1: (a1, a5 W^1, a9 W^2, a13 W^3); a5 W^1 +- a13 W^3 = c (o0 | o1)
+    const C b0 = a[1], q9 = a[9], q5 = a[5], q13 = a[13];
+    const R px = q9.x + q9.y, py = q9.y - q9.x;
+    C e0, e1;
+    e0.x = fmadd(h, px, b0.x);  e0.y = fmadd(h, py, b0.y);
+    e1.x = fmadd(-h, px, b0.x); e1.y = fmadd(-h, py, b0.y);
+    const R P = q5.x + q13.y, Q = q5.y + q13.x, Rr = q5.y - q13.x, S = q5.x - q13.y;
+    const R o0x = fmadd(t, Q, P), o0y = fmadd(-t, S, Rr);
+    const R o1x = fmadd(t, Rr, S), o1y = fmadd(-t, P, Q);
+    v[1].x = fmadd(c, o0x, e0.x);   v[1].y = fmadd(c, o0y, e0.y);
+    v[9].x = fmadd(-c, o0x, e0.x);  v[9].y = fmadd(-c, o0y, e0.y);
+    v[5].x = fmadd(c, o1y, e1.x);   v[5].y = fmadd(-c, o1x, e1.y);
+    v[13].x = fmadd(-c, o1y, e1.x); v[13].y = fmadd(c, o1x, e1.y);
+  }
+  {  // k1 = 3: (a3, a7 W^3, a11 W^6, a15 W^9); a7 W^3 +- a15 W^9 = c (o0 | o1)
+    const C b0 = a[3], q11 = a[11], q7 = a[7], q15 = a[15];
+    const R rx = q11.y - q11.x, ry = -q11.x - q11.y;
+    C e0, e1;
+    e0.x = fmadd(h, rx, b0.x);  e0.y = fmadd(h, ry, b0.y);
+    e1.x = fmadd(-h, rx, b0.x); e1.y = fmadd(-h, ry, b0.y);
+    const R P = q7.y - q15.x, Q = q7.x - q15.y, Rr = q7.x + q15.y, S = q7.y + q15.x;
+    const R o0x = fmadd(t, Q, P), o0y = fmadd(t, S, -Rr);
+    const R o1x = fmadd(t, Rr, S), o1y = fmadd(t, P, -Q);
+    v[3].x = fmadd(c, o0x, e0.x);   v[3].y = fmadd(c, o0y, e0.y);
+    v[11].x = fmadd(-c, o0x, e0.x); v[11].y = fmadd(-c, o0y, e0.y);
+    v[7].x = fmadd(c, o1y, e1.x);   v[7].y = fmadd(-c, o1x, e1.y);
+    v[15].x = fmadd(-c, o1y, e1.x); v[15].y = fmadd(c, o1x, e1.y);
+  }
+}
+
+// The inverse through the forward transform: with swap(a + ib) = b + ia,
+// IDFT(x) = swap(DFT(swap(x))); the swaps are register renames.
+template <bool INV, typename C>
+AAO_HD void dft16_fma(C* v) {
+  if constexpr (INV) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) { const auto r = v[i].x; v[i].x = v[i].y; v[i].y = r; }
+  }
+  dft16_fwd_fma(v);
+  if constexpr (INV) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) { const auto r = v[i].x; v[i].x = v[i].y; v[i].y = r; }
+  }
+}
+
+// Native fused multiply-add: the folded 16-point DFT is shorter.  In double-float
+// arithmetic a multiply-add is a product plus a sum, so there the folded form would
+// add products and the plain one is kept.
+template <typename C> struct FoldedDft16 { static constexpr bool value = true; };
+template <> struct FoldedDft16<dfl2> { static constexpr bool value = false; };
+
 template <int RX, bool INV, typename C>
 AAO_HD void dft_r(C* v) {
   if constexpr (RX == 2) { C a = v[0]; v[0] = cadd(a, v[1]); v[1] = csub(a, v[1]); }
   else if constexpr (RX == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
   else if constexpr (RX == 8) dft8<INV>(v);
+  else if constexpr (FoldedDft16<C>::value) dft16_fma<INV>(v);
   else dft16<INV>(v);
 }
 
