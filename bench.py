@@ -92,6 +92,11 @@ def algorithmic_flops(cls: str, d: int, N: int, nt: int, unknowns: int) -> float
         return unknowns * 2.5 * log2(M)
     if cls in ("yt", "yt_dot", "yt_res"):
         return unknowns * (2 * d + 3 + (1 if cls != "yt" else 0))
+    if cls == "wx_res":
+        # w and x updates (3 + 2 multiply-adds, one product: 7) and the DST-basis
+        # residual Lambda (x_i + x_{i-2}) - 2 x_{i-1}, its difference from b and its
+        # square accumulated (7)
+        return unknowns * 14
     return 0.0
 
 
@@ -110,6 +115,9 @@ def algorithmic_bytes(cls: str, d: int, N: int, nt: int, unknowns: int, vec_byte
         return 16 * unknowns
     if cls in ("yt_dot", "yt_res"):
         return 24 * unknowns
+    if cls == "wx_res":
+        # reads z, w_{j-1}, w_j, x, b; writes w_{j+1}, x
+        return 56 * unknowns
     return 0.0
 
 

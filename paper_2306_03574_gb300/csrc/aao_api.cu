@@ -32,13 +32,14 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 enum KClass {
   KC_DST_X64, KC_DST_Y64, KC_DST_Z64, KC_TIME64, KC_DST_X32, KC_DST_Y32, KC_DST_Z32, KC_TIME32,
   KC_YT, KC_YT_DOT, KC_YT_RES, KC_DOT, KC_VUPD, KC_WXUPD, KC_SCAL, KC_RHS, KC_SUB, KC_CAST,
-  KC_AXPY, KC_TABLE, KC_TIMEFF, KC_DST_XFF, KC_DST_YFF, KC_DST_ZFF, KC_N
+  KC_AXPY, KC_TABLE, KC_TIMEFF, KC_DST_XFF, KC_DST_YFF, KC_DST_ZFF, KC_WXRES, KC_N
 };
 const char* kc_name(int c) {
   static const char* names[KC_N] = {
       "dst_x_f64", "dst_y_f64", "dst_z_f64", "time_f64", "dst_x_f32", "dst_y_f32", "dst_z_f32",
       "time_f32", "yt", "yt_dot", "yt_res", "dot", "vupdate", "wxupdate", "scalars", "rhs", "sub",
-      "cast", "axpy", "spectral_table", "time_f32x2", "dst_x_f32x2", "dst_y_f32x2", "dst_z_f32x2"};
+      "cast", "axpy", "spectral_table", "time_f32x2", "dst_x_f32x2", "dst_y_f32x2", "dst_z_f32x2",
+      "wx_res"};
   return (c >= 0 && c < KC_N) ? names[c] : "other";
 }
 
@@ -412,6 +413,13 @@ aao_status minres_enqueue_iter(const MinresCtx& c, const MinresBufs& B) {
   AAO_TRY(c.prec(B.vp, B.zn));
   AAO_KL(h, KC_DOT, s, launch_dot(P, B.zn, B.vp, p1, nrhs, s, nl));
   AAO_KL(h, KC_SCAL, s, launch_scalars(2, h->sc, p1, nb_dot, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+  if (c.true_res && !c.physical) {
+    // DST basis: the update and the true residual of the new iterate in one pass
+    AAO_KL(h, KC_WXRES, s, launch_wx_res(P, h->lam64, B.z, B.wp, B.w, c.xh, c.bh, h->sc, p1, nrhs, s, nl,
+                                         &nb_yt));  // wp <- w_{j+1}
+    AAO_KL(h, KC_SCAL, s, launch_scalars(3, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+    return AAO_OK;
+  }
   AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, B.z, B.wp, B.w, c.xh, h->sc, nrhs, s, nl));  // wp <- w_{j+1}
   if (c.true_res) {
     AAO_KL(h, KC_YT_RES, s, c.op(c.xh, nullptr, c.bh, p1, 2, &nb_yt));
@@ -847,7 +855,7 @@ size_t aaoi_estimate_bytes(int dim, int N, int nt, int precision) {
   for (int i = 0; i < dim; ++i) m *= (size_t)N;
   const size_t npairs = (m + 1) / 2;
   const size_t vec = (size_t)nt * m * sizeof(double);
-  const size_t nbyt = ((m + 255) / 256) * (((size_t)nt + 31) / 32);
+  const size_t nbyt = std::max(((m + 255) / 256) * (((size_t)nt + 31) / 32), (m + 31) / 32);
   const size_t table = (size_t)(nt / 2 + 1) * npairs * 2 * sizeof(double2);  // FP64 (and dfl2) table
   return 9 * vec + (precision == AAO_PREC_F32X2 ? 2 : 1) * table + m * sizeof(double) +
          3 * std::max(nbyt, (size_t)296) * sizeof(double) + (1 << 16);
@@ -1000,7 +1008,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   if (fp32) {
     if ((st = h->alloc(&h->vr, vl)) || (st = h->alloc(&h->vdx, vl))) return bail(st);
   }
-  h->partial_stride = std::max(yt_blocks_per_rhs(P), dot_blocks_per_rhs(P));
+  h->partial_stride = std::max(std::max(yt_blocks_per_rhs(P), dot_blocks_per_rhs(P)), wxres_blocks_per_rhs(P));
   if ((st = h->alloc(&h->partial, (size_t)3 * h->nrhs_max * h->partial_stride)) ||
       (st = h->alloc(&h->sc, (size_t)h->nrhs_max)))
     return bail(st);

@@ -149,6 +149,12 @@ cudaError_t launch_vupdate(const Plan& P, const double* T, const double* v, doub
 cudaError_t launch_wxupdate(const Plan& P, const double* z, double* wprev_out, const double* w,
                             double* x, const MinresScalars* sc, int nrhs, cudaStream_t s,
                             uint64_t* nl);
+// launch_wxupdate fused with the true residual ||b - Y T^ x||^2 of the updated x in the DST
+// basis (partials [rhs][wxres_blocks_per_rhs], *nb = blocks per rhs); sc.done rhs untouched.
+cudaError_t launch_wx_res(const Plan& P, const double* lam, const double* z, double* wprev_out,
+                          const double* w, double* x, const double* b, const MinresScalars* sc,
+                          double* partial, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
+int wxres_blocks_per_rhs(const Plan& P);
 // y = x0 - x1 (used for r0 = b - A x0)
 cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* y, int nrhs,
                        cudaStream_t s, uint64_t* nl);

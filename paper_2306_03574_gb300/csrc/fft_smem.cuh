@@ -70,6 +70,24 @@ AAO_HD void dft4(C& v0, C& v1, C& v2, C& v3) {
   }
 }
 
+// Forward 4-point DFT of (s0 v0, s1 v1, s2 v2, s3 v3) for real s_r: the products of
+// the first butterflies' second operands are folded into multiply-adds (three
+// operations per component pair instead of four).
+template <typename C, typename R>
+AAO_HD void dft4_scaled_fwd(C& v0, C& v1, C& v2, C& v3, R s0, R s1, R s2, R s3) {
+  C p, q, a0, a1, a2, a3;
+  p.x = v0.x * s0; p.y = v0.y * s0;
+  q.x = v1.x * s1; q.y = v1.y * s1;
+  a0.x = fmadd(s2, v2.x, p.x);  a0.y = fmadd(s2, v2.y, p.y);
+  a1.x = fmadd(-s2, v2.x, p.x); a1.y = fmadd(-s2, v2.y, p.y);
+  a2.x = fmadd(s3, v3.x, q.x);  a2.y = fmadd(s3, v3.y, q.y);
+  a3.x = fmadd(-s3, v3.x, q.x); a3.y = fmadd(-s3, v3.y, q.y);
+  v0 = cadd(a0, a2);
+  v2 = csub(a0, a2);
+  v1.x = a1.x + a3.y; v1.y = a1.y - a3.x;  // a1 - i a3
+  v3.x = a1.x - a3.y; v3.y = a1.y + a3.x;  // a1 + i a3
+}
+
 // ---------------------------------------------------------------------------
 // Higher radices: in-register 8- and 16-point DFTs and a generic radix-RX
 // Stockham stage.  Fewer stages mean fewer shared-memory round trips and
@@ -155,9 +173,10 @@ AAO_HD void dft16(C* v) {
 // (-1 + i t), t = tan(pi/8).  The short factors cost additions or one multiply-add
 // each, and the common factor is applied by the multiply-adds that form the outputs
 // instead of by separate products: 144 real operations instead of 160.
-template <typename C>
-AAO_HD void dft16_fwd_fma(C* v) {
-  using R = decltype(v[0].x);
+// With SCALED, the input element r is first multiplied by the real factor sc[r] (the
+// diagonal scaling that precedes a transform), folded into the first butterflies.
+template <bool SCALED = false, typename C, typename R = decltype(C::x)>
+AAO_HD void dft16_fwd_fma(C* v, const R* sc = nullptr) {
   const R h = R(0.70710678118654752440);  // sqrt(2)/2
   const R c = R(0.92387953251128675613);  // cos(pi/8)
   const R t = R(0.41421356237309504880);  // tan(pi/8) = sqrt(2) - 1
@@ -165,7 +184,8 @@ AAO_HD void dft16_fwd_fma(C* v) {
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) {
     C x0 = v[n2], x1 = v[4 + n2], x2 = v[8 + n2], x3 = v[12 + n2];
-    dft4<false>(x0, x1, x2, x3);
+    if constexpr (SCALED) dft4_scaled_fwd(x0, x1, x2, x3, sc[n2], sc[4 + n2], sc[8 + n2], sc[12 + n2]);
+    else dft4<false>(x0, x1, x2, x3);
     a[4 * n2 + 0] = x0; a[4 * n2 + 1] = x1; a[4 * n2 + 2] = x2; a[4 * n2 + 3] = x3;
   }
   {  // k1 = 0: no twiddles
@@ -246,6 +266,20 @@ AAO_HD void dft_r(C* v) {
   else dft16<INV>(v);
 }
 
+// Forward radix-RX DFT (RX = 4 or 16) of the inputs scaled by real factors sc[r].
+template <int RX, typename C, typename R>
+AAO_HD void dft_r_scaled(C* v, const R* sc) {
+  static_assert(RX == 4 || RX == 16, "scaled first stages are radix 4 or 16");
+  if constexpr (FoldedDft16<C>::value) {
+    if constexpr (RX == 4) dft4_scaled_fwd(v[0], v[1], v[2], v[3], sc[0], sc[1], sc[2], sc[3]);
+    else dft16_fwd_fma<true>(v, sc);
+  } else {  // double-float: a multiply-add is no cheaper than a product and a sum
+#pragma unroll
+    for (int r = 0; r < RX; ++r) { v[r].x = v[r].x * sc[r]; v[r].y = v[r].y * sc[r]; }
+    dft_r<RX, false>(v);
+  }
+}
+
 // One radix-RX Stockham stage with span LS (sub-transforms of length LS done):
 // task j in [0, L/RX), k = j mod LS, v_r = x[j + r L/RX], v_r *= w^{r k L/(RX LS)},
 // DFT_RX, y[(j - k) RX + k + r LS] = v_r.  Every thread computes one base index for
@@ -307,6 +341,54 @@ __device__ __forceinline__ void fft_stage_r(C* buf, const C* tw) {
   else fft_stage_body<L, NS, NT, RX, INV, LAY, LS>(buf, tw);
 }
 
+// First stage (span 1, so no twiddles) of a forward transform whose input element x
+// is multiplied by the real factor sc[x] first: the diagonal scaling that precedes the
+// transform costs no pass of its own.
+template <int L, int NS, int NT, int RX, int LAY, typename C, typename R>
+__device__ __forceinline__ void fft_stage1_scaled_body(C* buf, const R* sc) {
+  using Y = SLay<L, NS, LAY>;
+  constexpr int Q = L / RX;
+  constexpr int TASKS = NS * Q;
+  static_assert(TASKS % NT == 0, "radix tasks must divide evenly among threads");
+  static_assert(Q % 16 == 0 || 16 % Q == 0, "read offsets");
+  static_assert(RX <= 16, "write offsets");
+  constexpr int TPT = TASKS / NT;
+  C v[TPT][RX];
+#pragma unroll
+  for (int t = 0; t < TPT; ++t) {
+    int q, j;
+    Y::template split<Q>(threadIdx.x + t * NT, q, j);
+    const C* p = buf + Y::at(q, j);
+#pragma unroll
+    for (int r = 0; r < RX; ++r) v[t][r] = p[Y::off(r * Q)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < TPT; ++t) {
+    int q, j;
+    Y::template split<Q>(threadIdx.x + t * NT, q, j);
+    R f[RX];
+#pragma unroll
+    for (int r = 0; r < RX; ++r) f[r] = sc[j + r * Q];
+    dft_r_scaled<RX>(v[t], f);
+    C* o = buf + Y::at(q, j * RX);
+#pragma unroll
+    for (int r = 0; r < RX; ++r) o[Y::off(r)] = v[t][r];
+  }
+  __syncthreads();
+}
+
+template <int L, int NS, int NT, int RX, int LAY, typename C, typename R>
+__device__ __noinline__ void fft_stage1_scaled_call(C* buf, const R* sc) {
+  fft_stage1_scaled_body<L, NS, NT, RX, LAY>(buf, sc);
+}
+
+template <int L, int NS, int NT, int RX, int LAY, typename C, typename R>
+__device__ __forceinline__ void fft_stage1_scaled(C* buf, const R* sc) {
+  if constexpr (StageCalled<C>::value) fft_stage1_scaled_call<L, NS, NT, RX, LAY>(buf, sc);
+  else fft_stage1_scaled_body<L, NS, NT, RX, LAY>(buf, sc);
+}
+
 // Radix-4 stage plan from span LS on, with one radix-2 stage last when log2(L) is odd.
 template <int L, int NS, int NT, bool INV, int LAY, int LS, typename C>
 __device__ __forceinline__ void fft_r4_from(C* buf, const C* tw) {
@@ -326,27 +408,40 @@ __device__ __forceinline__ void fft_block(C* buf, const C* tw) {
 }
 
 // Stage plans with radix-16 first: 64 = 16*4, 128 = 16*8, 256 = 16*16,
-// 512 = 16*16*2, 1024 = 16*16*4.
-template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
-__device__ __forceinline__ void fft_block16(C* buf, const C* tw) {
+// 512 = 16*16*2, 1024 = 16*16*4.  The stages after the first:
+template <int L, int NS, int NT, bool INV, int LAY, typename C>
+__device__ __forceinline__ void fft_block16_rest(C* buf, const C* tw) {
   if constexpr (L == 64) {
-    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
     fft_stage_r<L, NS, NT, 4, INV, LAY, 16>(buf, tw);
   } else if constexpr (L == 128) {
-    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
     fft_stage_r<L, NS, NT, 8, INV, LAY, 16>(buf, tw);
   } else if constexpr (L == 256) {
-    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
     fft_stage_r<L, NS, NT, 16, INV, LAY, 16>(buf, tw);
   } else if constexpr (L == 512) {
-    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
     fft_stage_r<L, NS, NT, 16, INV, LAY, 16>(buf, tw);
     fft_stage_r<L, NS, NT, 2, INV, LAY, 256>(buf, tw);
   } else {
-    fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
     fft_stage_r<L, NS, NT, 16, INV, LAY, 16>(buf, tw);
     fft_stage_r<L, NS, NT, 4, INV, LAY, 256>(buf, tw);
   }
+}
+
+template <int L, int NS, int NT, bool INV, int LAY = 0, typename C>
+__device__ __forceinline__ void fft_block16(C* buf, const C* tw) {
+  fft_stage_r<L, NS, NT, 16, INV, LAY, 1>(buf, tw);
+  fft_block16_rest<L, NS, NT, INV, LAY>(buf, tw);
+}
+
+// Forward transforms of diag(sc) x, the scaling folded into the first stage.
+template <int L, int NS, int NT, int LAY = 0, typename C, typename R>
+__device__ __forceinline__ void fft_block_scaled(C* buf, const C* tw, const R* sc) {
+  fft_stage1_scaled<L, NS, NT, 4, LAY>(buf, sc);
+  fft_r4_from<L, NS, NT, false, LAY, 4>(buf, tw);
+}
+template <int L, int NS, int NT, int LAY = 0, typename C, typename R>
+__device__ __forceinline__ void fft_block16_scaled(C* buf, const C* tw, const R* sc) {
+  fft_stage1_scaled<L, NS, NT, 16, LAY>(buf, sc);
+  fft_block16_rest<L, NS, NT, false, LAY>(buf, tw);
 }
 
 }  // namespace aao

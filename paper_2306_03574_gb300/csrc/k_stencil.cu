@@ -33,8 +33,9 @@ __device__ __forceinline__ double apply_L(const double* __restrict__ v, int s, i
   return fma(-a.coef, sum, a.diag * v[s]);
 }
 
+template <int NT = YT_NT>
 __device__ __forceinline__ double block_sum(double v) {
-  __shared__ double red[YT_NT / 32];
+  __shared__ double red[NT / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -42,7 +43,7 @@ __device__ __forceinline__ double block_sum(double v) {
   __syncthreads();
   double t = 0.0;
   if (w == 0) {
-    t = (l < YT_NT / 32) ? red[l] : 0.0;
+    t = (l < NT / 32) ? red[l] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   }
@@ -133,6 +134,66 @@ __global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, d
       partial[blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
   }
+}
+
+// One MINRES step's direction and iterate update fused with the true residual, in the
+// DST basis (Section 3's stopping test on the system whose operator is pointwise in s):
+//   w_{j+1} = c0 z + c1 w_{j-1} + c2 w_j (written over w_{j-1}),   x += c3 w_{j+1},
+//   r_{n-1-i} = b_{n-1-i} - (Lambda_s (x_i + x_{i-2}) - 2 x_{i-1}),  partial = sum r^2,
+// with (c0..c3) = sc[rhs].cw.  A block owns WXR_S consecutive spatial modes and all n
+// time levels of them, split into WXR_C runs of n/WXR_C levels, one thread per mode
+// and run.  A run needs the updated x at the two levels before it, which the thread of
+// the previous run overwrites in place; every thread therefore recomputes those two
+// values (the same operations on the same inputs, so bit for bit the same) before a
+// barrier, and only then starts writing.  Converged right-hand sides (sc.done) are
+// left untouched and their partial is not written.
+constexpr int WXR_S = 32;
+constexpr int WXR_C = 4;
+constexpr int WXR_NT = WXR_S * WXR_C;
+
+__global__ void __launch_bounds__(WXR_NT) k_wx_res(const double* __restrict__ z, double* __restrict__ wprev,
+                                                   const double* __restrict__ w, double* __restrict__ x,
+                                                   const double* __restrict__ b, const double* __restrict__ lam,
+                                                   const MinresScalars* __restrict__ sc,
+                                                   double* __restrict__ partial, int n, int m) {
+  const MinresScalars& S = sc[blockIdx.y];
+  if (S.done) return;  // uniform over the block
+  const int s = blockIdx.x * WXR_S + (int)(threadIdx.x % WXR_S);
+  const int len = n / WXR_C;
+  const int i0 = (int)(threadIdx.x / WXR_S) * len;
+  const bool on = s < m;
+  const double c0 = S.cw[0], c1 = S.cw[1], c2 = S.cw[2], c3 = S.cw[3];
+  const long long rb = (long long)blockIdx.y * n * m + s;
+  const double* zp = z + rb;
+  double* wpp = wprev + rb;
+  const double* wq = w + rb;
+  double* xp = x + rb;
+  const double* bp = b + rb + (long long)(n - 1) * m;  // b at time slot n-1-i is bp[-i m]
+  double x1 = 0.0, x2 = 0.0;                           // updated x_{i-1}, x_{i-2}
+  if (on && i0 > 0) {
+    const long long o2 = (long long)(i0 - 2) * m, o1 = o2 + m;
+    x2 = fma(c3, fma(c0, zp[o2], fma(c1, wpp[o2], c2 * wq[o2])), xp[o2]);
+    x1 = fma(c3, fma(c0, zp[o1], fma(c1, wpp[o1], c2 * wq[o1])), xp[o1]);
+  }
+  __syncthreads();
+  double acc = 0.0;
+  if (on) {
+    const double ls = lam[s];
+#pragma unroll 4
+    for (int i = i0; i < i0 + len; ++i) {
+      const long long o = (long long)i * m;
+      const double wn = fma(c0, zp[o], fma(c1, wpp[o], c2 * wq[o]));
+      wpp[o] = wn;
+      const double xi = fma(c3, wn, xp[o]);
+      xp[o] = xi;
+      const double r = fma(-ls, xi + x2, fma(2.0, x1, bp[-o]));
+      acc = fma(r, r, acc);
+      x2 = x1;
+      x1 = xi;
+    }
+  }
+  const double t = block_sum<WXR_NT>(acc);
+  if (threadIdx.x == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 // Variable coefficient: L_a w(s) = w(s) + cv sum_axes [aR (w(s) - w(s+e)) + aL (w(s) - w(s-e))],
@@ -284,6 +345,18 @@ YtArgs make_args(const Plan& P) {
 }
 
 }  // namespace
+
+int wxres_blocks_per_rhs(const Plan& P) { return (P.m + WXR_S - 1) / WXR_S; }
+
+cudaError_t launch_wx_res(const Plan& P, const double* lam, const double* z, double* wprev_out,
+                          const double* w, double* x, const double* b, const MinresScalars* sc,
+                          double* partial, int nrhs, cudaStream_t s, uint64_t* nl, int* nb) {
+  if (nl) ++*nl;
+  const dim3 g(wxres_blocks_per_rhs(P), nrhs);
+  if (nb) *nb = (int)g.x;
+  k_wx_res<<<g, WXR_NT, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m);
+  return cudaGetLastError();
+}
 
 int yt_blocks_per_rhs(const Plan& P) {
   return ((P.m + YT_NT - 1) / YT_NT) * ((P.n + YT_CH - 1) / YT_CH);

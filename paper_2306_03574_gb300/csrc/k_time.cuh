@@ -111,12 +111,29 @@ __device__ __forceinline__ void fft_run(C* buf, const C* tw) {
   if constexpr (FFTV == 0) fft_block<L, NS, NT, INV, LAY>(buf, tw);
   else fft_block16<L, NS, NT, INV, LAY>(buf, tw);
 }
+// Forward FFT of diag(sc) x (the D^{-1} and D^2 scalings ride on the first stage)
+template <int FFTV, int L, int NS, int NT, int LAY, typename C, typename R>
+__device__ __forceinline__ void fft_run_scaled(C* buf, const C* tw, const R* sc) {
+  if constexpr (FFTV == 0) fft_block_scaled<L, NS, NT, LAY>(buf, tw, sc);
+  else fft_block16_scaled<L, NS, NT, LAY>(buf, tw, sc);
+}
+
+// Where the D^{-1} and D^2 scalings go: into the first stage of the forward FFTs
+// (multiply-adds, one shared-memory pass fewer) in FP64, whose kernel is bound by the
+// FP64 pipe, and in FP32 up to n = 256; at n >= 512 the FP32 kernel needs more
+// registers for the folded stage and loses a resident CTA per SM, which costs more than
+// the pass (measured), and in double-float a multiply-add saves nothing.  Otherwise the
+// load applies D^{-1} and a separate pass D^2.
+template <typename R, int L> struct FoldScaling { static constexpr bool value = false; };
+template <int L> struct FoldScaling<double, L> { static constexpr bool value = true; };
+template <int L> struct FoldScaling<float, L> { static constexpr bool value = L <= 256; };
 
 template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
   using Y = SLay<L, NS, LAY>;
   constexpr bool STAGED = LAY == 1;
+  constexpr bool FOLD = FoldScaling<R, L>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cbuf = reinterpret_cast<C*>(smem_raw);
   C* tab = cbuf + Y::size;                           // staged table slice (STAGED only)
@@ -137,33 +154,38 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
   }
   __syncthreads();
 
-  // load and scale by D^{-1}
+  // load, scaled by D^{-1} here or (FOLD) by the first FFT stage
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
     const int sa = s0 + 2 * q;
     const TIO* p = in + rb + (long long)t * m + sa;
-    const R di = dinv[t];
+    const R di = FOLD ? R(1) : dinv[t];
     C z;
-    z.x = (sa < m) ? R(p[0]) * di : R();
-    z.y = (sa + 1 < m) ? R(p[1]) * di : R();
+    z.x = (sa < m) ? (FOLD ? R(p[0]) : R(p[0]) * di) : R();
+    z.y = (sa + 1 < m) ? (FOLD ? R(p[1]) : R(p[1]) * di) : R();
     cbuf[Y::at(q, t)] = z;
   }
   if constexpr (STAGED) cp_async_wait_all();
   __syncthreads();
 
-  fft_run<FFTV, L, NS, NT, false, LAY>(cbuf, tw);
+  if constexpr (FOLD) fft_run_scaled<FFTV, L, NS, NT, LAY>(cbuf, tw, dinv);
+  else fft_run<FFTV, L, NS, NT, false, LAY>(cbuf, tw);
   mix_pass<false, L, NS, NT, LAY, STAGED>(cbuf, tb.ab, tab, a.npairs, p0);
   fft_run<FFTV, L, NS, NT, true, LAY>(cbuf, tw);
-  for (int task = tid; task < NS * L; task += NT) {
-    const int q = task % NS, t = task / NS;
-    const int i = Y::at(q, t);
-    C z = cbuf[i];
-    z.x *= d2[t];
-    z.y *= d2[t];
-    cbuf[i] = z;
+  if constexpr (FOLD) {
+    fft_run_scaled<FFTV, L, NS, NT, LAY>(cbuf, tw, d2);
+  } else {
+    for (int task = tid; task < NS * L; task += NT) {
+      const int q = task % NS, t = task / NS;
+      const int i = Y::at(q, t);
+      C z = cbuf[i];
+      z.x *= d2[t];
+      z.y *= d2[t];
+      cbuf[i] = z;
+    }
+    __syncthreads();
+    fft_run<FFTV, L, NS, NT, false, LAY>(cbuf, tw);
   }
-  __syncthreads();
-  fft_run<FFTV, L, NS, NT, false, LAY>(cbuf, tw);
   mix_pass<true, L, NS, NT, LAY, STAGED>(cbuf, tb.ab, tab, a.npairs, p0);
   fft_run<FFTV, L, NS, NT, true, LAY>(cbuf, tw);
 
