@@ -604,9 +604,9 @@ def run_gpu(args, world, rank, local):
         fl = algorithmic_flops(cls, d, p.N, p.nt, unknowns)
         if cls.endswith("f32x2"):  # counted as the FP32 operations of the double-word algorithms
             fl *= DW_FP32_FLOPS_PER_FLOP
-        by = algorithmic_bytes(cls, d, p.N, p.nt, unknowns,
-                               8 if cls.endswith("f64") or cls.startswith("yt") or cls.endswith("f32x2") else vb32)
-        alu_peak = FP64_PEAK_TFLOPS if cls.endswith("f64") or cls.startswith("yt") else FP32_PEAK_TFLOPS
+        fp64_cls = cls.endswith("f64") or cls.startswith("yt") or cls == "wx_res"
+        by = algorithmic_bytes(cls, d, p.N, p.nt, unknowns, 8 if fp64_cls or cls.endswith("f32x2") else vb32)
+        alu_peak = FP64_PEAK_TFLOPS if fp64_cls else FP32_PEAK_TFLOPS
         t = kern[cls]["avg_ms"] / 1e3
         # the binding roofline: whichever of the ALU and HBM times is longer
         if fl / (alu_peak * 1e12) >= by / (hbm * 1e9):
