@@ -81,7 +81,7 @@ def log2(v):
     return v.bit_length() - 1
 
 
-def algorithmic_flops(cls: str, d: int, N: int, nt: int, unknowns: int) -> float:
+def algorithmic_flops(cls: str, d: int, N: int, nt: int, unknowns: int, varcoef: bool = False) -> float:
     """Algorithmic FLOPs of one launch of a kernel class (standard FFT count
     5 L log2 L per complex transform of length L, i.e. 2.5 L log2 L per real one)."""
     M = N + 1
@@ -92,8 +92,20 @@ def algorithmic_flops(cls: str, d: int, N: int, nt: int, unknowns: int) -> float
     if cls.startswith("dst"):
         # DST-I of length N counted as one real transform of length N+1
         return unknowns * 2.5 * log2(M)
-    if cls in ("yt", "yt_dot", "yt_res"):
-        return unknowns * (2 * d + 3 + (1 if cls != "yt" else 0))
+    if cls.startswith("yt"):
+        # Y T v per unknown.  With a constant coefficient, MINRES runs in the DST basis,
+        # where the operator is Lambda (v_i + v_{i-2}) - 2 v_{i-1} (4 flops); the
+        # physical residual check applies the stencil L (2d neighbours summed, scaled
+        # and subtracted from the scaled centre: 2d + 2) and the time band (3).  The
+        # variable-coefficient operator takes 6d + 1 per L application (face-weighted
+        # differences) plus the time band.  A fused dot adds 2, a residual 3.
+        if varcoef:
+            op = 6 * d + 4
+        elif cls == "yt_res":
+            op = 2 * d + 5
+        else:
+            op = 4
+        return unknowns * (op + (2 if cls == "yt_dot" else 3 if cls == "yt_res" else 0))
     if cls == "wx_res":
         # w and x updates (3 + 2 multiply-adds, one product: 7) and the DST-basis
         # residual Lambda (x_i + x_{i-2}) - 2 x_{i-1}, its difference from b and its
@@ -113,10 +125,10 @@ def algorithmic_bytes(cls: str, d: int, N: int, nt: int, unknowns: int, vec_byte
         return 2 * vec_bytes * unknowns + (nt // 2 + 1) * ((m + 1) // 2) * 2 * csize
     if cls.startswith("dst"):
         return 2 * vec_bytes * unknowns
-    if cls == "yt":
+    if cls in ("yt", "yt_dot", "yt_res"):
+        # one vector in and one out (the fused dot's operand is the input itself; the
+        # residual reads b instead of writing)
         return 16 * unknowns
-    if cls in ("yt_dot", "yt_res"):
-        return 24 * unknowns
     if cls == "wx_res":
         # reads z, w_{j-1}, w_j, x, b; writes w_{j+1}, x
         return 56 * unknowns
@@ -603,7 +615,7 @@ def run_gpu(args, world, rank, local):
     vb32 = 4 if varcoef else 8
 
     def roof(cls):
-        fl = algorithmic_flops(cls, d, p.N, p.nt, unknowns)
+        fl = algorithmic_flops(cls, d, p.N, p.nt, unknowns, varcoef)
         if cls.endswith("f32x2"):  # counted as the FP32 operations of the double-word algorithms
             fl *= DW_FP32_FLOPS_PER_FLOP
         fp64_cls = cls.endswith("f64") or cls.startswith("yt") or cls == "wx_res"
@@ -633,7 +645,7 @@ def run_gpu(args, world, rank, local):
             variants["dst_variant"] if dom.startswith("dst") else None)
     roofline["traffic"] = traffic_record(dom, var)
     for k in kern:
-        if algorithmic_flops(k, d, p.N, p.nt, unknowns):
+        if algorithmic_flops(k, d, p.N, p.nt, unknowns, varcoef):
             r = roof(k)
             kern[k].update(bound=r["bound"], achieved=r["achieved"], unit=r["unit"], frac=r["frac"])
     # preconditioner application as a whole, against HBM (16 B per unknown in + out)

@@ -85,6 +85,7 @@ struct aao_handle {
   cudaStream_t cap_stream = nullptr;
   int* d_trips = nullptr;
   int* trips_host = nullptr;  // pinned
+  double* d_prm = nullptr;    // rtol, maxit of the solve a graph launch runs
   struct GraphCache {
     long key;
     double rtol;
@@ -353,6 +354,7 @@ struct MinresCtx {
   int maxit;
   cudaStream_t s;
   bool true_res, physical;
+  const double* prm = nullptr;  // graph capture: rtol, maxit read from device memory
   cudaError_t op(const double* xx, double* yy, const double* ww, double* part, int mode, int* nbp) const {
     return physical ? launch_op(h, xx, yy, ww, part, mode, nrhs, s, nbp)
                     : launch_ythat(h->P, h->lam64, xx, yy, ww, part, mode, nrhs, s, &h->launches, nbp);
@@ -392,7 +394,7 @@ aao_status minres_enqueue_init(const MinresCtx& c, int use_x0, const MinresBufs&
   AAO_KL(h, KC_DOT, s, launch_dot(P, c.bh, c.bh, p2, c.nrhs, s, nl));
   AAO_KL(h, KC_DOT, s, launch_dot(P, B.v, B.v, p3, c.nrhs, s, nl));
   AAO_KL(h, KC_SCAL, s, launch_scalars(0, h->sc, p1, nb_dot, p2, nb_dot, p3, nb_dot, c.nrhs, c.rtol,
-                                       c.maxit, s, nl));
+                                       c.maxit, s, nl, c.prm));
   return AAO_OK;
 }
 
@@ -460,6 +462,7 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   MinresCtx cc = c;
   cudaStream_t cs = h->cap_stream;
   cc.s = cs;
+  cc.prm = h->d_prm;  // rtol and maxit are set before each launch, not captured
   const MinresBufs B0{h->vv, h->vvp, h->vz, h->vzn, h->vw, h->vwp};
   const int trip_limit = c.maxit / 2 + 2;
   cudaGraph_t g = nullptr;
@@ -482,7 +485,7 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamBeginCaptureToGraph");
   if (cudaMemsetAsync(h->d_trips, 0, sizeof(int), cs) != cudaSuccess ||
       minres_enqueue_init(cc, use_x0, B0) != AAO_OK ||
-      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 0, cs, &h->launches) != cudaSuccess) {
+      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 0, cs, &h->launches, h->d_prm) != cudaSuccess) {
     h->launches = l0;
     return fail_cleanup(cudaGetLastError(), "graph initialisation capture");
   }
@@ -511,7 +514,7 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   if (e != cudaSuccess) return fail_cleanup(e, "capture of the loop body");
   const MinresBufs B1 = rotate(B0);
   if (minres_enqueue_iter(cc, B0) != AAO_OK || minres_enqueue_iter(cc, B1) != AAO_OK ||
-      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 1, cs, &h->launches) != cudaSuccess) {
+      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 1, cs, &h->launches, h->d_prm) != cudaSuccess) {
     h->launches = l0;
     return fail_cleanup(cudaGetLastError(), "loop body capture");
   }
@@ -544,14 +547,15 @@ aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_
   const size_t scb = (size_t)nrhs * sizeof(MinresScalars);
   const MinresBufs B0{h->vv, h->vvp, h->vz, h->vzn, h->vw, h->vwp};
   if (h->use_graph && !h->prof_on) {
-    // rtol and maxit live in the device scalars, written by the captured initialisation
-    // from the values below; the graph is keyed on everything else.
+    // rtol and maxit go to device memory ahead of the launch and the captured
+    // initialisation and loop condition read them there; the graph is keyed on the rest.
     cudaGraphExec_t ex = nullptr;
     if (get_graph(c, use_x0, &ex) != AAO_OK) {
       // keep solving with the host-driven loop (aao_last_error keeps the reason)
       h->use_graph = false;
       return minres_spectral(h, bh, xh, use_x0, nrhs, rtol, maxit, info, s, true_res, physical);
     }
+    AAO_CK(launch_set_params(h->d_prm, rtol, maxit, s, &h->launches));
     AAO_CK(cudaGraphLaunch(ex, s));
     AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
     AAO_CK(cudaMemcpyAsync(h->trips_host, h->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -792,7 +796,7 @@ aao_status get_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   const long key = ((long)c.nrhs << 8) | (use_x0 ? 1 : 0) | (c.true_res ? 2 : 0) | (c.physical ? 4 : 0) |
                    ((c.bh == h->vr) ? 8 : 0);
   for (auto& gc : h->graphs)
-    if (gc.key == key && gc.rtol == c.rtol && gc.maxit == c.maxit) {
+    if (gc.key == key) {  // rtol and maxit are device parameters of the graph
       *out = gc.exec;
       h->last_init_kernels = gc.init_kernels;
       h->last_body_kernels = gc.body_kernels;
@@ -827,6 +831,7 @@ aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double 
   MinresCtx c{h, h->vbh, h->vxh, 1, rtol, maxit, s, true, false};
   cudaGraphExec_t ex = nullptr;
   AAO_TRY(get_graph(c, 0, &ex));
+  AAO_CK(launch_set_params(h->d_prm, rtol, maxit, s, &h->launches));
   AAO_CK(cudaGraphLaunch(ex, s));
   AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(MinresScalars), cudaMemcpyDeviceToHost, s));
   AAO_CK(cudaMemcpyAsync(h->trips_host, h->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -988,7 +993,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     return bail(st);
   if (o.graph) {
     h->use_graph = true;
-    if ((st = h->alloc(&h->d_trips, 1))) return bail(st);
+    if ((st = h->alloc(&h->d_trips, 1)) || (st = h->alloc(&h->d_prm, 2))) return bail(st);
     if (cudaMallocHost(&h->trips_host, sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       h->trips_host = nullptr;

@@ -163,10 +163,16 @@ cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* 
 // 3 = true residual check (partial = sum r^2), 4 = recurrence-estimate check (no partial)
 cudaError_t launch_scalars(int step, MinresScalars* sc, const double* partial, int nb,
                            const double* partial2, int nb2, const double* partial3, int nb3,
-                           int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl);
+                           int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl,
+                           const double* prm = nullptr);
 // Graph WHILE-loop control: trips += count; condition = (any rhs not done) && trips < limit.
+// With prm, the limit is prm[1]/2 + 2 (and step 0 of launch_scalars takes rtol = prm[0],
+// maxit = prm[1]), so one captured graph serves every tolerance and iteration limit.
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle hw, const MinresScalars* sc, int nrhs, int* trips,
-                             int trip_limit, int count, cudaStream_t s, uint64_t* nl);
+                             int trip_limit, int count, cudaStream_t s, uint64_t* nl,
+                             const double* prm = nullptr);
+// prm[0] = rtol, prm[1] = maxit (stream-ordered, ahead of a graph launch)
+cudaError_t launch_set_params(double* prm, double rtol, int maxit, cudaStream_t s, uint64_t* nl);
 // relres[r] = sqrt(sum of p1 partials / sum of p2 partials) per right-hand side
 cudaError_t launch_relres(const double* p1, int nb1, const double* p2, int nb2, double* relres,
                           int nrhs, cudaStream_t s, uint64_t* nl);

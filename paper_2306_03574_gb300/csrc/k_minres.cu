@@ -72,6 +72,11 @@ __global__ void __launch_bounds__(VNT) k_wxupdate(const double* __restrict__ z, 
   }
 }
 
+__global__ void k_set_params(double* prm, double rtol, int maxit) {
+  prm[0] = rtol;
+  prm[1] = (double)maxit;
+}
+
 __global__ void __launch_bounds__(VNT) k_sub(const double* __restrict__ a, const double* __restrict__ b,
                                              double* __restrict__ y, long long len) {
   for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT)
@@ -105,7 +110,7 @@ __device__ __forceinline__ double sum_partials(const double* p, int nb) {
 
 __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict__ p1, int nb1,
                           const double* __restrict__ p2, int nb2, const double* __restrict__ p3,
-                          int nb3, double rtol, int maxit) {
+                          int nb3, double rtol, int maxit, const double* __restrict__ prm) {
   const int r = blockIdx.x;
   MinresScalars& S = sc[r];
   const double s1 = sum_partials(p1 + (long long)r * nb1, nb1);
@@ -116,9 +121,9 @@ __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict_
   }
   if (threadIdx.x != 0) return;
   if (step == 0) {
-    // s1 = <z1, v1>, s2 = <b, b>, s3 = <v1, v1>
-    S.rtol = rtol;
-    S.maxit = maxit;
+    // s1 = <z1, v1>, s2 = <b, b>, s3 = <v1, v1>; rtol and maxit from prm when given
+    S.rtol = prm ? prm[0] : rtol;
+    S.maxit = prm ? (int)prm[1] : maxit;
     S.iters = 0;
     S.status = AAO_OK;
     S.done = 0;
@@ -217,8 +222,9 @@ __global__ void k_relres(const double* __restrict__ p1, int nb1, const double* _
 // the WHILE condition to "some right-hand side still iterating and trips < limit"
 // (the limit bounds the loop whatever the scalar state holds).
 __global__ void k_loop_cond(cudaGraphConditionalHandle hw, const MinresScalars* __restrict__ sc, int nrhs,
-                            int* trips, int trip_limit, int count) {
+                            int* trips, int trip_limit, int count, const double* __restrict__ prm) {
   if (threadIdx.x != 0) return;
+  if (prm) trip_limit = (int)prm[1] / 2 + 2;  // two iterations per trip
   const int t = *trips + count;
   *trips = t;
   bool any = false;
@@ -271,9 +277,15 @@ cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* 
 }
 
 cudaError_t launch_loop_cond(cudaGraphConditionalHandle hw, const MinresScalars* sc, int nrhs, int* trips,
-                             int trip_limit, int count, cudaStream_t s, uint64_t* nl) {
+                             int trip_limit, int count, cudaStream_t s, uint64_t* nl, const double* prm) {
   if (nl) ++*nl;
-  k_loop_cond<<<1, 32, 0, s>>>(hw, sc, nrhs, trips, trip_limit, count);
+  k_loop_cond<<<1, 32, 0, s>>>(hw, sc, nrhs, trips, trip_limit, count, prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_params(double* prm, double rtol, int maxit, cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  k_set_params<<<1, 1, 0, s>>>(prm, rtol, maxit);
   return cudaGetLastError();
 }
 
@@ -314,9 +326,10 @@ cudaError_t launch_axpy(double a, const double* x, double* y, size_t count, cuda
 
 cudaError_t launch_scalars(int step, MinresScalars* sc, const double* partial, int nb,
                            const double* partial2, int nb2, const double* partial3, int nb3,
-                           int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl) {
+                           int nrhs, double rtol, int maxit, cudaStream_t s, uint64_t* nl,
+                           const double* prm) {
   if (nl) ++*nl;
-  k_scalars<<<nrhs, 32, 0, s>>>(step, sc, partial, nb, partial2, nb2, partial3, nb3, rtol, maxit);
+  k_scalars<<<nrhs, 32, 0, s>>>(step, sc, partial, nb, partial2, nb2, partial3, nb3, rtol, maxit, prm);
   return cudaGetLastError();
 }
 
