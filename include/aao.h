@@ -82,9 +82,11 @@ typedef struct aao_opts {
   int nrhs_max;          /* largest batch passed to any call; workspace is sized for it (default 1) */
   int variable_coefficient; /* != 0: reserve room for a coefficient set by aao_set_coefficient */
   int graph;             /* != 0: aao_minres_solve captures its iteration loop once per (batch
-                            size, tolerance, maxit) into a CUDA graph whose device-side WHILE
+                            size, initial-guess use) into a CUDA graph whose device-side WHILE
                             node runs the iterations without host round trips (bounded by
-                            maxit); when kernel timing is enabled the host-driven loop is used */
+                            maxit); tolerance and maxit are written to device memory before
+                            each launch, so they may change between calls without a new
+                            capture; when kernel timing is enabled the host-driven loop is used */
   int reserved[4];       /* must be zero */
 } aao_opts;
 
