@@ -19,7 +19,7 @@ namespace aao {
 
 namespace {
 constexpr int VNT = 256;
-constexpr int DOT_BLOCKS = 296;  // partial sums per right-hand side (2 per SM)
+constexpr int DOT_BLOCKS = 608;  // partial sums per right-hand side (4 per SM)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(VNT) k_dot(const double* __restrict__ a, const
                                              double* __restrict__ partial, long long len) {
   const long long rb = (long long)blockIdx.y * len;
   double acc = 0.0;
+#pragma unroll 4
   for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT)
     acc = fma(a[rb + i], c[rb + i], acc);
   __shared__ double red[VNT / 32];
@@ -45,25 +46,27 @@ __global__ void __launch_bounds__(VNT) k_dot(const double* __restrict__ a, const
 }
 
 __global__ void __launch_bounds__(VNT) k_vupdate(const double* __restrict__ T, const double* __restrict__ v,
-                                                 double* vprev, const MinresScalars* __restrict__ sc,
+                                                 double* __restrict__ vprev, const MinresScalars* __restrict__ sc,
                                                  long long len) {
   const MinresScalars& S = sc[blockIdx.y];
   const long long rb = (long long)blockIdx.y * len;
   const bool dn = S.done != 0;
   const double c0 = S.cv[0], c1 = S.cv[1], c2 = S.cv[2];
+#pragma unroll 4
   for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT) {
     const long long k = rb + i;
     vprev[k] = dn ? 0.0 : fma(c0, T[k], fma(c1, v[k], c2 * vprev[k]));
   }
 }
 
-__global__ void __launch_bounds__(VNT) k_wxupdate(const double* __restrict__ z, double* wprev,
+__global__ void __launch_bounds__(VNT) k_wxupdate(const double* __restrict__ z, double* __restrict__ wprev,
                                                   const double* __restrict__ w, double* __restrict__ x,
                                                   const MinresScalars* __restrict__ sc, long long len) {
   const MinresScalars& S = sc[blockIdx.y];
   if (S.done) return;
   const long long rb = (long long)blockIdx.y * len;
   const double c0 = S.cw[0], c1 = S.cw[1], c2 = S.cw[2], c3 = S.cw[3];
+#pragma unroll 4
   for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT) {
     const long long k = rb + i;
     const double wn = fma(c0, z[k], fma(c1, wprev[k], c2 * w[k]));

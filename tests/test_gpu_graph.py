@@ -77,6 +77,35 @@ def test_graph_variable_coefficient_and_maxit():
     assert got[0][4] == got[1][4] == 3
 
 
+def test_graph_tolerance_and_maxit_per_call():
+    """rtol and maxit reach the captured graph through device memory: one graph handle
+    alternating tolerances and iteration limits stops exactly where the host-driven
+    loop does, call after call."""
+    d, N, nt = 2, 63, 128
+    x = W.random_field((nt, N * N), seed=1450)
+    calls = [(1e-6, 100), (1e-11, 100), (1e-11, 2), (1e-6, 100), (1e-9, 3)]
+    out = []
+    for graph in (False, True):
+        with aao.Solver(d, N, nt, 1.0 / nt, 1e-6, graph=graph) as s:
+            xt = cu(x)
+            b = torch.empty_like(xt)
+            s.apply_op(xt, b)
+            res = []
+            for rtol, maxit in calls:
+                y = torch.empty_like(xt)
+                st, info = s.solve(b, y, rtol=rtol, maxit=maxit)
+                torch.cuda.synchronize()
+                res.append((st, info[0]["iters"], info[0]["relres_true"], y.cpu().numpy()))
+            out.append(res)
+    for (st0, it0, r0, y0), (st1, it1, r1, y1), (rtol, maxit) in zip(out[0], out[1], calls):
+        assert st0 == st1 and it0 == it1 and r0 == r1, (rtol, maxit)
+        assert np.array_equal(y0, y1)
+        assert it1 <= maxit
+        assert (st1 == aao.AAO_OK) == (r1 <= rtol)
+    assert out[1][2][0] == aao.AAO_ENOTCONV and out[1][2][1] == 2
+    assert out[1][0][1] < out[1][1][1]          # the looser tolerance stops earlier
+
+
 def test_autotune_keeps_results_and_caches(tmp_path):
     """The autotuner only changes speed: after tuning, P^{-1} and the solve still match
     the oracle; the tune file is written and then read back."""
