@@ -650,7 +650,7 @@ def run_gpu(args, world, rank, local):
             kern[k].update(bound=r["bound"], achieved=r["achieved"], unit=r["unit"], frac=r["frac"])
     # preconditioner application as a whole, against HBM (16 B per unknown in + out)
     prec_cls = [k for k in kern if k.startswith("dst") or k.startswith("time") or k == "cast"]
-    applies = kern.get("time_f64", kern.get("time_f32", kern.get("time_f32x2", {}))).get("launches", 0)
+    applies = sum(v["launches"] for k, v in kern.items() if k.startswith("time"))
     prec_ms = sum(kern[k]["total_ms"] for k in prec_cls) / max(applies, 1)
     prec = {"ms_per_apply": prec_ms, "algorithmic_bytes": 16 * unknowns,
             "hbm_gbs": 16 * unknowns / (prec_ms / 1e3) / 1e9 if prec_ms else None}

@@ -105,10 +105,16 @@ __global__ void __launch_bounds__(VNT) k_axpy(double a, const double* __restrict
 }
 
 // deterministic sum of nb partials of right-hand side r by one warp
+// (eight independent running sums per lane keep eight loads in flight; fixed order)
 __device__ __forceinline__ double sum_partials(const double* p, int nb) {
-  double t = 0.0;
-  for (int i = threadIdx.x; i < nb; i += 32) t += p[i];
-  return warp_sum(t);
+  double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int i = threadIdx.x;
+  for (; i + 7 * 32 < nb; i += 8 * 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] += p[i + 32 * u];
+  }
+  for (; i < nb; i += 32) t[0] += p[i];
+  return warp_sum(((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7])));
 }
 
 __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict__ p1, int nb1,
