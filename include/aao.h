@@ -319,7 +319,8 @@ const char* aao_serve_last_error(void);
 /* Autotuner: pick, for this handle's shape and precision, the fastest variant of the
  * time-pipeline kernel (FFT stage plan: radix-4 or radix-16 first; tile: 4096/n or
  * 2048/n mode pairs per CTA; shared-memory layout: sequence-major or interleaved and
- * padded) and of the DST kernel (radix-4 or radix-16 stage plan) by
+ * padded, the latter with or without a staged slice of the spectral table in
+ * double-float mode) and of the DST kernel (radix-4 or radix-16 stage plan) by
  * timing each on the handle's workspace with CUDA events (the work of the kernels is
  * the same in every variant; only speed differs).  The default variant is kept unless
  * another is more than 1 % faster, so near-ties give the same choice on every run.

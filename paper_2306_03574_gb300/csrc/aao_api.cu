@@ -936,7 +936,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     if (sscanf(tv, "%d,%d,%d", &a, &b, &c) >= 1) {
       P.time_variant64 = a & 7;
       P.time_variant32 = (b >= 0 ? b : a) & 7;
-      P.time_variant_ff = (c >= 0 ? c : (b >= 0 ? b : a)) & 7;
+      P.time_variant_ff = (c >= 0 ? c : (b >= 0 ? b : a)) & 15;
     }
   }
   if (const char* dv = getenv("AAO_DST_VARIANT")) P.dst_variant = atoi(dv) & 1;
@@ -1077,7 +1077,7 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
       bool found = false;
       while (fscanf(fh, "%d %d %d %d %d %d", &d, &N, &n, &pr, &tv, &dv) == 6)
         if (d == P.d && N == P.N && n == P.n && pr == prec) {
-          tvar(P, prec) = tv & 7;
+          tvar(P, prec) = tv & (prec == AAO_PREC_F32X2 ? 15 : 7);
           P.dst_variant = dv & 1;
           found = true;
         }
@@ -1116,8 +1116,10 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // The default variants stay unless another is faster by more than 1 % (run-to-run
   // timing noise is a few tenths of a percent; near-ties keep the choice reproducible).
   const int def_tv = tvar(P, prec), def_dv = P.dst_variant;
-  std::vector<float> tt(8), td(2);
-  for (int v = 0; v < 8; ++v) {
+  // double-float has four more time variants (8..11: interleaved layout, no staged table)
+  const int ntv = prec == AAO_PREC_F32X2 ? 12 : 8;
+  std::vector<float> tt(ntv), td(2);
+  for (int v = 0; v < ntv; ++v) {
     tvar(P, prec) = v;
     tt[v] = timeit([&]() {
       if (prec == AAO_PREC_FP64) launch_time<double>(P, h->vv, h->vz, 1, s, nullptr);
@@ -1126,7 +1128,7 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
     });
   }
   int best_tv = 0;
-  for (int v = 1; v < 8; ++v)
+  for (int v = 1; v < ntv; ++v)
     if (tt[v] < tt[best_tv]) best_tv = v;
   if (!(tt[best_tv] < 0.99f * tt[def_tv])) best_tv = def_tv;
   tvar(P, prec) = best_tv;

@@ -66,7 +66,7 @@ struct Plan {
   // in shared memory.  Defaults measured on GB300: FP64 (FP64-pipe bound) radix-16 +
   // half tile; FP32 radix-16 + full tile + interleaved layout (bank conflicts and
   // table-load latency dominate otherwise).
-  int time_variant64 = 3, time_variant32 = 5, time_variant_ff = 5;
+  int time_variant64 = 3, time_variant32 = 5, time_variant_ff = 9;
   // DST stage plan: 0 = radix-4, 1 = radix-16 first
   int dst_variant = 1;
   PrecTables<double> t64;

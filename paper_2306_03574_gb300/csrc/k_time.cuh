@@ -21,7 +21,9 @@
 // and padded, see fft_smem.cuh).  The interleaved variants also stage the CTA's
 // slice of the spectral table in shared memory with asynchronous copies issued
 // before the input load, so both spectral multiplies read it from there and its
-// global-memory latency overlaps the load.  All variants compute the same values;
+// global-memory latency overlaps the load.  Double-float has four more, 8..11 (bit 3):
+// the interleaved layout without the staged slice, whose 16-byte table entries would
+// otherwise take a third of the shared memory and one resident CTA per SM.  All variants compute the same values;
 // the translation units k_time64.cu / k_time32.cu instantiate them per precision.
 #pragma once
 #include <type_traits>
@@ -128,11 +130,11 @@ template <typename R, int L> struct FoldScaling { static constexpr bool value = 
 template <int L> struct FoldScaling<double, L> { static constexpr bool value = true; };
 template <int L> struct FoldScaling<float, L> { static constexpr bool value = L <= 256; };
 
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY>
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
   using Y = SLay<L, NS, LAY>;
-  constexpr bool STAGED = LAY == 1;
+  constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
   constexpr bool FOLD = FoldScaling<R, L>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cbuf = reinterpret_cast<C*>(smem_raw);
@@ -202,16 +204,17 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
 }
 
 // Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY>
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1>
 static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
-  const size_t smem = sizeof(C) * (SLay<L, NS, LAY>::size + (LAY ? 2 * NS * (L / 2 + 1) : 0) + L) +
+  constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
+  const size_t smem = sizeof(C) * (SLay<L, NS, LAY>::size + (STAGED ? 2 * NS * (L / 2 + 1) : 0) + L) +
                       2 * sizeof(R) * L;
   TimeArgs a;
   a.m = P.m;
   a.n = P.n;
   a.npairs = P.npairs;
-  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY>;
+  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY, STG>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
   kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
@@ -223,6 +226,16 @@ static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrh
   const int v = std::is_same<R, double>::value  ? P.time_variant64
                 : std::is_same<R, float>::value ? P.time_variant32
                                                 : P.time_variant_ff;
+  if constexpr (std::is_same<R, dfl>::value) {
+    if (v & 8) {  // interleaved layout without the staged table slice
+      switch (v & 3) {
+        case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0, 1, 0>(P, in, out, nrhs, s);
+        case 1: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, 0>(P, in, out, nrhs, s);
+        case 2: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 0, 1, 0>(P, in, out, nrhs, s);
+        default: return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, 0>(P, in, out, nrhs, s);
+      }
+    }
+  }
   switch (v & 7) {
     case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0, 0>(P, in, out, nrhs, s);
     case 1: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 0>(P, in, out, nrhs, s);
