@@ -92,6 +92,10 @@ def algorithmic_flops(cls: str, d: int, N: int, nt: int, unknowns: int, varcoef:
     if cls.startswith("dst"):
         # DST-I of length N counted as one real transform of length N+1
         return unknowns * 2.5 * log2(M)
+    if cls == "yt_resvec":
+        # refinement residual in the DST basis: the operator (4), b minus it (1), its
+        # square accumulated (2)
+        return unknowns * 7
     if cls.startswith("yt"):
         # Y T v per unknown.  With a constant coefficient, MINRES runs in the DST basis,
         # where the operator is Lambda (v_i + v_{i-2}) - 2 v_{i-1} (4 flops); the
@@ -129,6 +133,9 @@ def algorithmic_bytes(cls: str, d: int, N: int, nt: int, unknowns: int, vec_byte
         # one vector in and one out (the fused dot's operand is the input itself; the
         # residual reads b instead of writing)
         return 16 * unknowns
+    if cls == "yt_resvec":
+        # reads x and b, writes r
+        return 24 * unknowns
     if cls == "wx_res":
         # reads z, w_{j-1}, w_j, x, b; writes w_{j+1}, x
         return 56 * unknowns

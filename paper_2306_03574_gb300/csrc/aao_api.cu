@@ -32,14 +32,14 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 enum KClass {
   KC_DST_X64, KC_DST_Y64, KC_DST_Z64, KC_TIME64, KC_DST_X32, KC_DST_Y32, KC_DST_Z32, KC_TIME32,
   KC_YT, KC_YT_DOT, KC_YT_RES, KC_DOT, KC_VUPD, KC_WXUPD, KC_SCAL, KC_RHS, KC_SUB, KC_CAST,
-  KC_AXPY, KC_TABLE, KC_TIMEFF, KC_DST_XFF, KC_DST_YFF, KC_DST_ZFF, KC_WXRES, KC_N
+  KC_AXPY, KC_TABLE, KC_TIMEFF, KC_DST_XFF, KC_DST_YFF, KC_DST_ZFF, KC_WXRES, KC_RESV, KC_N
 };
 const char* kc_name(int c) {
   static const char* names[KC_N] = {
       "dst_x_f64", "dst_y_f64", "dst_z_f64", "time_f64", "dst_x_f32", "dst_y_f32", "dst_z_f32",
       "time_f32", "yt", "yt_dot", "yt_res", "dot", "vupdate", "wxupdate", "scalars", "rhs", "sub",
       "cast", "axpy", "spectral_table", "time_f32x2", "dst_x_f32x2", "dst_y_f32x2", "dst_z_f32x2",
-      "wx_res"};
+      "wx_res", "yt_resvec"};
   return (c >= 0 && c < KC_N) ? names[c] : "other";
 }
 
@@ -664,19 +664,22 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
   const int max_ir = 40;
   int total_its = 0;
   for (int ir = 0; ir < max_ir; ++ir) {
-    // r^ = b^ - Y T^ x^ in FP64 and its norm
-    int nb_yt = 0;
-    if (phys) AAO_KL(h, KC_YT, s, launch_op(h, xh, h->vT, nullptr, nullptr, 0, nrhs, s, &nb_yt));
-    else AAO_KL(h, KC_YT, s, launch_ythat(P, h->lam64, xh, h->vT, nullptr, nullptr, 0, nrhs, s, nl, &nb_yt));
-    AAO_KL(h, KC_SUB, s, launch_sub(P, bh, h->vT, h->vr, nrhs, s, nl));
-    AAO_KL(h, KC_DOT, s, launch_dot(P, h->vr, h->vr, p1, nrhs, s, nl));
-    AAO_CK(cudaMemcpyAsync(hp.data(), p1, (size_t)nrhs * nb_dot * sizeof(double), cudaMemcpyDeviceToHost, s));
+    // r^ = b^ - Y T^ x^ in FP64 and its norm (one fused pass in the DST basis)
+    int nb_yt = 0, nb_r = nb_dot;
+    if (phys) {
+      AAO_KL(h, KC_YT, s, launch_op(h, xh, h->vT, nullptr, nullptr, 0, nrhs, s, &nb_yt));
+      AAO_KL(h, KC_SUB, s, launch_sub(P, bh, h->vT, h->vr, nrhs, s, nl));
+      AAO_KL(h, KC_DOT, s, launch_dot(P, h->vr, h->vr, p1, nrhs, s, nl));
+    } else {
+      AAO_KL(h, KC_RESV, s, launch_ythat(P, h->lam64, xh, h->vr, bh, p1, 3, nrhs, s, nl, &nb_r));
+    }
+    AAO_CK(cudaMemcpyAsync(hp.data(), p1, (size_t)nrhs * nb_r * sizeof(double), cudaMemcpyDeviceToHost, s));
     AAO_CK(cudaStreamSynchronize(s));
     bool all = true;
     double worst_rel = 0.0;
     for (int r = 0; r < nrhs; ++r) {
       double t = 0;
-      for (int i = 0; i < nb_dot; ++i) t += hp[(size_t)r * nb_dot + i];
+      for (int i = 0; i < nb_r; ++i) t += hp[(size_t)r * nb_r + i];
       const double rel = std::sqrt(t) / bn[r];
       acc[r].relres_true = rel;
       acc[r].ir_steps = ir;

@@ -96,7 +96,8 @@ cudaError_t launch_time(const Plan& P, const R* in, R* out, int nrhs, cudaStream
 cudaError_t launch_yt(const Plan& P, const double* x, double* y, const double* w, double* partial,
                       int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
 int yt_blocks_per_rhs(const Plan& P);
-// The operator in the DST basis (L -> diag(lam)); same modes and partial layout as launch_yt.
+// The operator in the DST basis (L -> diag(lam)); same modes and partial layout as launch_yt,
+// plus mode 3: y = w - Y T^ x written out, partials of ||y||^2.
 cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, double* y, const double* w,
                          double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
 // Time pipeline computed in FP32/complex64 on FP64 vectors (conversion in the load and store).

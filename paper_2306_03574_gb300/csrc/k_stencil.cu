@@ -95,7 +95,9 @@ __global__ void __launch_bounds__(YT_NT) k_yt(const double* __restrict__ x, doub
 
 // The same operator in the DST basis: with U = S (x)..(x) S orthogonal and symmetric,
 // (I (x) U) Y T (I (x) U) is Y T with L replaced by diag(Lambda), so
-// (Y T^ v)_{n-1-i} = Lambda_s (v_i + v_{i-2}) - 2 v_{i-1} pointwise in s.  Modes as k_yt.
+// (Y T^ v)_{n-1-i} = Lambda_s (v_i + v_{i-2}) - 2 v_{i-1} pointwise in s.  Modes as k_yt,
+// plus mode 3: the residual vector y = w - Y T^ v written out with the sum of its squares
+// (the refinement loop's r = b - A x and ||r||^2 in one pass).
 template <int MODE>
 __global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, double* __restrict__ y,
                                                  const double* __restrict__ w,
@@ -116,10 +118,11 @@ __global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, d
       if (i >= i0) {
         const double o = fma(-2.0, x1, ls * (xi + x2));
         const long long idx = rb + (long long)(n - 1 - i) * m + s;
-        if (MODE != 2) y[idx] = o;
+        if (MODE == 0 || MODE == 1) y[idx] = o;
         if (MODE == 1) acc = fma(o, w[idx], acc);
-        if (MODE == 2) {
+        if (MODE >= 2) {
           const double r = w[idx] - o;
+          if (MODE == 3) y[idx] = r;
           acc = fma(r, r, acc);
         }
       }
@@ -393,7 +396,8 @@ cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, doub
   if (nb) *nb = (int)(g.x * g.y);
   if (mode == 0) k_ythat<0><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
   else if (mode == 1) k_ythat<1><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
-  else k_ythat<2><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
+  else if (mode == 2) k_ythat<2><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
+  else k_ythat<3><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
   return cudaGetLastError();
 }
 
