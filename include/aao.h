@@ -87,7 +87,10 @@ typedef struct aao_opts {
                             maxit); tolerance and maxit are written to device memory before
                             each launch, so they may change between calls without a new
                             capture; when kernel timing is enabled the host-driven loop is used */
-  int reserved[4];       /* must be zero */
+  int host_staging;      /* != 0: aao_create also reserves the device buffers, copy stream and
+                            events of aao_solve_host (for nrhs_max right-hand sides), so that no
+                            later call allocates; 0: the first aao_solve_host reserves them */
+  int reserved[3];       /* must be zero */
 } aao_opts;
 
 typedef struct aao_solve_info {
@@ -103,7 +106,8 @@ typedef struct aao_handle aao_handle;
 
 /* Create a solver for one (grid, nt, tau, alpha) and allocate all its device
  * memory (tables + workspace); this is the only allocating call besides the
- * serving API.  Builds, on the device, the spectral factors
+ * serving API and, for a handle created without opts.host_staging, the first
+ * aao_solve_host.  Builds, on the device, the spectral factors
  * Sigma_{k,j}^{-1/2} = (Lambda_j lambda_{1,k} + lambda_{2,k})^{-1/2} with the
  * principal branch (eqs. (calphaprediagform), (calphasqrtdiagform); Section 2.3).
  *   grid  : host pointer; dim in {1,2,3}; N+1 a power of two, 64 <= N+1 <= 512
@@ -116,8 +120,14 @@ typedef struct aao_handle aao_handle;
  *   scheme: AAO_SCHEME_IMPLICIT_LEAPFROG.
  *   opts  : host pointer or NULL for defaults.
  *   out   : receives the handle (host pointer).
- * Synchronous on the current device.  Errors: AAO_EINVAL, AAO_EUNSUPPORTED,
- * AAO_ENOMEM, AAO_ECUDA, AAO_ESINGULAR. */
+ * The tables are built on a non-blocking stream owned by the handle, and the call
+ * returns once that stream is done: it does not wait for work that other streams
+ * have in flight on the device.
+ * Tuning overrides (environment, read here; for measurements and tests):
+ *   AAO_TIME_VARIANT="v64[,v32[,vff]]" sets the time-kernel variant per precision
+ *   (the numbering of aao_autotune; a missing entry repeats the previous one), and
+ *   AAO_DST_VARIANT="0|1" the DST stage plan.  Every variant computes the same values.
+ * Errors: AAO_EINVAL, AAO_EUNSUPPORTED, AAO_ENOMEM, AAO_ECUDA, AAO_ESINGULAR. */
 aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha,
                       aao_scheme scheme, const aao_opts* opts, aao_handle** out);
 
@@ -163,8 +173,8 @@ aao_status aao_apply_op(aao_handle* h, const double* x, double* y, int nrhs, voi
  * mode the time pipeline D^{-1} -> FFT -> x Sigma^{-1/2} -> iFFT -> D^2 ->
  * FFT -> x conj(Sigma^{-1/2}) -> iFFT -> D^{-1}, then the DSTs again.
  * r, z: nrhs x n x m device vectors; z may equal r (in place).  Uses the
- * handle's precision (in FP32 mode the first call allocates an FP32 staging vector
- * of nrhs_max x n x m floats).  Errors: AAO_EINVAL, AAO_ECUDA, AAO_ENOMEM. */
+ * handle's precision (in FP32 mode through an FP32 buffer of nrhs_max x n x m floats
+ * that aao_create reserves).  Errors: AAO_EINVAL, AAO_ECUDA. */
 aao_status aao_apply_prec(aao_handle* h, const double* r, double* z, int nrhs, void* stream);
 
 /* y = (I_n (x) U) x with U = S (x) ... (x) S the orthonormal multi-dimensional
@@ -220,10 +230,15 @@ aao_status aao_residual_norm(aao_handle* h, const double* b, const double* x, do
  *   b, x          : nrhs x n x m device vectors (inputs); relres: nrhs device doubles (output).
  *   nrhs          : 1..64.  Larger values return AAO_EINVAL: the scratch is a static
  *                   device array of 32768 doubles (256 KiB, 512 partial sums per
- *                   right-hand side) that every GPU loading the library holds until exit.
+ *                   right-hand side).
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls share the array and it keeps the last call's
+ * (cudaGetSymbolAddress) with the device current.  Under CUDA's lazy module loading
+ * (the default) that lookup also loads the array and its kernels onto the device, a
+ * one-time driver allocation of about 256 KiB plus code that stays until the process
+ * exits: make the first call at initialisation time, before any stream capture and
+ * before the caller's allocator takes the device's memory; later calls allocate
+ * nothing.  The looked-up address does not survive cudaDeviceReset: after a reset
+ * the entry point must not be called again.  All calls share the array and it keeps the last call's
  * partial sums (each call rewrites every slot it reads, so nothing needs
  * clearing); calls whose kernels overlap on the GPU (different streams, or
  * different host threads) race on it and must be serialised by the caller.
@@ -240,9 +255,10 @@ const char* aao_noalloc_last_error(void);
  * For constant-coefficient FP64 and double-float handles the copies run on a
  * second stream in chunks of 32 time levels, overlapping the right-hand side and
  * the DSTs (each level of those depends on its own f level only; the result is
- * bit for bit the device-buffer solve).  The first call allocates the device
- * copies of f, b, x and the copy stream.  Blocks until u is on the host.  Errors
- * as aao_minres_solve, and AAO_ENOMEM. */
+ * bit for bit the device-buffer solve).  The device copies of f, b, x, the copy
+ * stream and its events are reserved by aao_create if opts.host_staging was set,
+ * else by the first call (which then allocates).  Blocks until u is on the host.
+ * Errors as aao_minres_solve, and AAO_ENOMEM. */
 aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, const double* psi1,
                           double* u, int nrhs, double rtol, int maxit,
                           aao_solve_info* info, void* stream);
@@ -285,6 +301,9 @@ typedef struct aao_serve_stats {
   uint64_t submitted, admitted, completed, failed, handles_created, evictions;
   uint64_t pool_bytes, peak_pool_bytes, budget;
   int in_flight, pending;
+  uint64_t rounds;           /* grouped MINRES iterations run (one per size class and step) */
+  uint64_t round_problems;   /* requests summed over those rounds (/ rounds = mean group size) */
+  uint64_t grouped_launches; /* kernel launches of those rounds */
 } aao_serve_stats;
 
 /* Start a server on the current device.  hbm_budget_bytes bounds the device memory

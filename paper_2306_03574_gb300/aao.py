@@ -47,7 +47,7 @@ class aao_grid(ctypes.Structure):
 class aao_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("nrhs_max", ctypes.c_int),
                 ("variable_coefficient", ctypes.c_int), ("graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("host_staging", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class aao_solve_info(ctypes.Structure):
@@ -77,7 +77,8 @@ class aao_serve_stats_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "failed",
                                                "handles_created", "evictions", "pool_bytes",
                                                "peak_pool_bytes", "budget")] + \
-               [("in_flight", ctypes.c_int), ("pending", ctypes.c_int)]
+               [("in_flight", ctypes.c_int), ("pending", ctypes.c_int)] + \
+               [(n, ctypes.c_uint64) for n in ("rounds", "round_problems", "grouped_launches")]
 
 
 class aao_kernel_stat(ctypes.Structure):
@@ -214,10 +215,11 @@ def aao_last_error() -> str:
 
 def aao_create(dim: int, N: int, nt: int, tau: float, alpha: float, c2: float = 1.0,
                precision: int = AAO_PREC_FP64, nrhs_max: int = 1, scheme: int = 0,
-               raw_status: bool = False, variable_coefficient: bool = False, graph: bool = False):
+               raw_status: bool = False, variable_coefficient: bool = False, graph: bool = False,
+               host_staging: bool = False):
     g = aao_grid(dim, N, c2)
     o = aao_opts(precision, nrhs_max, int(bool(variable_coefficient)), int(bool(graph)),
-                 (ctypes.c_int * 4)())
+                 int(bool(host_staging)), (ctypes.c_int * 3)())
     h = ctypes.c_void_p()
     st = lib().aao_create(ctypes.byref(g), nt, tau, alpha, scheme, ctypes.byref(o), ctypes.byref(h))
     if raw_status:
@@ -246,6 +248,7 @@ def aao_workspace_bytes(h) -> int:
 
 def aao_launch_count(h) -> int:
     return int(lib().aao_launch_count(h))
+
 
 
 def aao_build_rhs(h, f, psi0, psi1, b, nrhs: int = 1, stream=None) -> None:
@@ -367,12 +370,13 @@ class Solver:
     """Owns one handle: `Solver(dim, N, nt, tau, alpha, ...)`; methods map 1:1 to the C calls."""
 
     def __init__(self, dim, N, nt, tau, alpha, c2=1.0, precision=AAO_PREC_FP64, nrhs_max=1,
-                 variable_coefficient=False, graph=False):
+                 variable_coefficient=False, graph=False, host_staging=False):
         self.dim, self.N, self.nt, self.tau, self.alpha, self.c2 = dim, N, nt, tau, alpha, c2
         self.m = N ** dim
         self.nrhs_max = nrhs_max
         self.h = aao_create(dim, N, nt, tau, alpha, c2, precision, nrhs_max,
-                            variable_coefficient=variable_coefficient, graph=graph)
+                            variable_coefficient=variable_coefficient, graph=graph,
+                            host_staging=host_staging)
 
     def autotune(self, tune_file=None) -> dict:
         return aao_autotune(self.h, tune_file)

@@ -80,6 +80,9 @@ struct aao_handle {
   double* face = nullptr;                        // variable coefficient on the faces (optional)
   bool var_on = false;                           // operator uses the face coefficients
   double* vxh = nullptr;                         // solution in the solve's working basis
+  // the handle's own non-blocking stream: table builds in aao_create and re-binds run on
+  // it, so creating or re-binding a handle never waits for work on other streams
+  cudaStream_t own_stream = nullptr;
   // graph-captured solves
   bool use_graph = false;
   cudaStream_t cap_stream = nullptr;
@@ -103,6 +106,11 @@ struct aao_handle {
   double* hs_f = nullptr; double* hs_psi = nullptr; double* hs_b = nullptr; double* hs_x = nullptr;
   cudaStream_t hs_copy = nullptr;    // copy stream of the pipelined host-buffer solve
   std::vector<cudaEvent_t> hs_ev;    // its chunk events (created on first use)
+  // serving: pinned host staging of an asynchronous re-bind (aaoi_serving_prepare)
+  void* pin = nullptr;
+  double2* pin_wq = nullptr; double* pin_dinv = nullptr; double* pin_d2 = nullptr; double* pin_lam = nullptr;
+  dfl* pin_dinv_ff = nullptr; dfl* pin_d2_ff = nullptr; double* pin_mm = nullptr;
+  int pin_nb = 0;  // spectral-table blocks of the last asynchronous re-bind (0: none pending)
   // kernel timing
   bool prof_on = false;
   std::vector<ProfRec> prof;
@@ -125,6 +133,7 @@ struct aao_handle {
   ~aao_handle() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (own_stream) cudaStreamDestroy(own_stream);
     if (hs_copy) cudaStreamDestroy(hs_copy);
     for (cudaEvent_t e : hs_ev) cudaEventDestroy(e);
     clear_prof();
@@ -133,6 +142,7 @@ struct aao_handle {
     if (sc_host) cudaFreeHost(sc_host);
     if (relres_host) cudaFreeHost(relres_host);
     if (trips_host) cudaFreeHost(trips_host);
+    if (pin) cudaFreeHost(pin);
   }
   template <typename T>
   aao_status alloc(T** p, size_t count) {
@@ -191,12 +201,6 @@ void host_twiddles(int L, int sign, std::vector<double2>& out) {
   }
 }
 
-template <typename T>
-aao_status upload(const std::vector<T>& h, T* d) {
-  AAO_CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return AAO_OK;
-}
-
 // stream-ordered upload from (pageable) host memory; the caller synchronises the stream
 template <typename T>
 aao_status upload_on(const std::vector<T>& h, T* d, cudaStream_t s) {
@@ -238,6 +242,26 @@ aao_status check_call(aao_handle* h, int nrhs) {
   return AAO_OK;
 }
 
+// Device buffers of aao_solve_host (f, b, x, psi0 and psi1 for nrhs_max right-hand
+// sides), its copy stream and its chunk events: reserved by aao_create when
+// opts.host_staging is set, else by the first aao_solve_host.
+constexpr int HOST_CHUNK = 32;  // time levels per pipelined copy chunk (n is a power of two >= 64)
+aao_status reserve_host_staging(aao_handle* h) {
+  const size_t vl = (size_t)h->nrhs_max * h->vlen();
+  AAO_TRY(h->alloc(&h->hs_f, vl));
+  AAO_TRY(h->alloc(&h->hs_b, vl));
+  AAO_TRY(h->alloc(&h->hs_x, vl));
+  AAO_TRY(h->alloc(&h->hs_psi, (size_t)2 * h->nrhs_max * h->P.m));
+  AAO_CK(cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking));
+  const int nch = h->nrhs_max * (h->P.n / HOST_CHUNK);
+  while ((int)h->hs_ev.size() < 2 * nch + 2) {
+    cudaEvent_t e = nullptr;
+    AAO_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->hs_ev.push_back(e);
+  }
+  return AAO_OK;
+}
+
 // P^{-1} applied in the handle's precision: in -> out (FP64 vectors, may alias)
 aao_status prec_apply(aao_handle* h, const double* in, double* out, int nrhs, cudaStream_t s) {
   const Plan& P = h->P;
@@ -257,7 +281,6 @@ aao_status prec_apply(aao_handle* h, const double* in, double* out, int nrhs, cu
       AAO_KL(h, KC_DST_XFF + ax, s, launch_dst_axis_ff(P, out, out, ax, nrhs, s, &h->launches));
   } else {
     const size_t cnt = (size_t)nrhs * h->vlen();
-    if (!h->f32) AAO_TRY(h->alloc(&h->f32, (size_t)h->nrhs_max * h->vlen()));  // first FP32 apply_prec
     AAO_KL(h, KC_CAST, s, launch_cast(in, h->f32, cnt, s, &h->launches));
     for (int ax = 0; ax < P.d; ++ax)
       AAO_KL(h, KC_DST_X32 + ax, s, launch_dst_axis<float>(P, h->f32, h->f32, ax, nrhs, s, &h->launches));
@@ -716,20 +739,17 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
   return worst;
 }
 
-// Parameter-dependent tables of a handle: D_alpha, D_alpha^2, the per-frequency terms
-// of Sigma, Lambda, and the spectral table (built on the device); checks min |Sigma|.
-// Used by aao_create and to re-bind a pooled handle to new (tau, alpha, c2).
-aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaStream_t s) {
-  Plan& P = h->P;
+// Parameter-dependent host tables of a handle for (tau, alpha, c2): the per-frequency
+// terms of Sigma (wq, 2n), D_alpha^{-1} and D_alpha^2 (n each) and Lambda (m), computed in
+// long double and rounded; also sets the plan's tau, alpha, c2 and stencil coefficient.
+void param_tables(Plan& P, double tau, double alpha, double c2, double2* wq, double* dinv, double* d2,
+                  double* lam) {
   const int nt = P.n, M = P.M;
-  const bool fp32 = (h->precision == AAO_PREC_FP32_IR);
   P.tau = tau;
   P.alpha = alpha;
   P.c2 = c2;
   P.coef = c2 * tau * tau / (2.0 * P.h * P.h);
   const long double pi = 3.141592653589793238462643383279502884L;
-  std::vector<double2> wq(2 * (size_t)nt);
-  std::vector<double> dinv(nt), d2(nt);
   const long double la = logl((long double)alpha);
   {
     // per-frequency terms of Sigma = (1 - a theta^k)^2 + (Lambda - 1)(1 + a^2 theta^{2k})
@@ -754,7 +774,6 @@ aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaSt
     const long double sv = sinl((long double)(i + 1) * pi * hl / 2.0L);
     mul[i] = 4.0L / (hl * hl) * sv * sv;
   }
-  std::vector<double> lam((size_t)P.m);
   const long double ct = 0.5L * (long double)c2 * (long double)tau * (long double)tau;
   for (long long s_ = 0; s_ < P.m; ++s_) {
     long long rest = s_;
@@ -762,27 +781,39 @@ aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaSt
     for (int ax = 0; ax < P.d; ++ax) { sum += mul[rest % P.N]; rest /= P.N; }
     lam[(size_t)s_] = (double)(1.0L + ct * sum);
   }
-  const std::vector<float> dinv32 = to_f(dinv), d232 = to_f(d2);
-  AAO_TRY(upload_on(dinv, h->dinv64, s));
-  AAO_TRY(upload_on(d2, h->d264, s));
-  AAO_TRY(upload_on(wq, h->d_wq, s));
-  AAO_TRY(upload_on(lam, h->lam64, s));
+}
+
+// Device side of a (re-)bind, stream-ordered on s from host arrays (pinned for a truly
+// asynchronous copy): uploads, the spectral table (and its double-float split), and the
+// per-block min/max |Sigma| copied to mm_host (nblocks pairs).
+aao_status bind_tables(aao_handle* h, const double2* wq, const double* dinv, const double* d2,
+                       const double* lam, const float* dinv32, const float* d232, const dfl* dinv_ff,
+                       const dfl* d2_ff, double* mm_host, int* nblocks, cudaStream_t s) {
+  Plan& P = h->P;
+  const size_t nt = (size_t)P.n;
+  const bool fp32 = (h->precision == AAO_PREC_FP32_IR);
+  AAO_CK(cudaMemcpyAsync(h->dinv64, dinv, nt * sizeof(double), cudaMemcpyHostToDevice, s));
+  AAO_CK(cudaMemcpyAsync(h->d264, d2, nt * sizeof(double), cudaMemcpyHostToDevice, s));
+  AAO_CK(cudaMemcpyAsync(h->d_wq, wq, 2 * nt * sizeof(double2), cudaMemcpyHostToDevice, s));
+  AAO_CK(cudaMemcpyAsync(h->lam64, lam, (size_t)P.m * sizeof(double), cudaMemcpyHostToDevice, s));
   if (fp32) {
-    AAO_TRY(upload_on(dinv32, h->dinv32, s));
-    AAO_TRY(upload_on(d232, h->d232, s));
+    AAO_CK(cudaMemcpyAsync(h->dinv32, dinv32, nt * sizeof(float), cudaMemcpyHostToDevice, s));
+    AAO_CK(cudaMemcpyAsync(h->d232, d232, nt * sizeof(float), cudaMemcpyHostToDevice, s));
   }
   if (h->precision == AAO_PREC_F32X2) {
-    AAO_TRY(upload_on(to_df(dinv), h->dinv_ff, s));
-    AAO_TRY(upload_on(to_df(d2), h->d2_ff, s));
+    AAO_CK(cudaMemcpyAsync(h->dinv_ff, dinv_ff, nt * sizeof(dfl), cudaMemcpyHostToDevice, s));
+    AAO_CK(cudaMemcpyAsync(h->d2_ff, d2_ff, nt * sizeof(dfl), cudaMemcpyHostToDevice, s));
   }
-  int nb = 0;
-  AAO_CK(launch_spectral_table(P, h->d_mu, h->d_wq, h->ab64, fp32 ? h->ab32 : nullptr, h->d_mm, &nb,
+  AAO_CK(launch_spectral_table(P, h->d_mu, h->d_wq, h->ab64, fp32 ? h->ab32 : nullptr, h->d_mm, nblocks,
                                s, &h->launches));
   if (h->precision == AAO_PREC_F32X2)
     AAO_CK(launch_split_df(h->ab64, h->ab_ff, (size_t)(P.n / 2 + 1) * P.npairs * 2, s, &h->launches));
-  std::vector<double> mm((size_t)2 * nb);
-  AAO_CK(cudaMemcpyAsync(mm.data(), h->d_mm, mm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-  AAO_CK(cudaStreamSynchronize(s));
+  AAO_CK(cudaMemcpyAsync(mm_host, h->d_mm, (size_t)2 * *nblocks * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return AAO_OK;
+}
+
+// min |Sigma| against max |Sigma| from the per-block pairs (Remark c1badperformremark)
+aao_status check_sigma(const double* mm, int nb) {
   double smin = 1e300, smax = 0.0;
   for (int i = 0; i < nb; ++i) {
     smin = std::min(smin, mm[2 * i]);
@@ -792,6 +823,25 @@ aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaSt
     return fail(AAO_ESINGULAR, "min |Sigma| / max |Sigma| = " + std::to_string(smin / smax) +
                                    " below 1e-12: preconditioner singular");
   return AAO_OK;
+}
+
+// Parameter-dependent tables of a handle: D_alpha, D_alpha^2, the per-frequency terms
+// of Sigma, Lambda, and the spectral table (built on the device); checks min |Sigma|.
+// Used by aao_create (synchronous on stream s).
+aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaStream_t s) {
+  Plan& P = h->P;
+  const int nt = P.n;
+  std::vector<double2> wq(2 * (size_t)nt);
+  std::vector<double> dinv(nt), d2(nt), lam((size_t)P.m);
+  param_tables(P, tau, alpha, c2, wq.data(), dinv.data(), d2.data(), lam.data());
+  const std::vector<float> dinv32 = to_f(dinv), d232 = to_f(d2);
+  const std::vector<dfl> dinv_ff = to_df(dinv), d2_ff = to_df(d2);
+  std::vector<double> mm((size_t)2 * h->mm_blocks);
+  int nb = 0;
+  AAO_TRY(bind_tables(h, wq.data(), dinv.data(), d2.data(), lam.data(), dinv32.data(), d232.data(),
+                      dinv_ff.data(), d2_ff.data(), mm.data(), &nb, s));
+  AAO_CK(cudaStreamSynchronize(s));  // pageable host arrays: wait before they go
+  return check_sigma(mm.data(), nb);
 }
 
 aao_status get_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
@@ -819,7 +869,7 @@ aao_status aaoi_rebind(aao_handle* h, double tau, double alpha, double c2) {
   if (!(tau > 0.0) || !(alpha > 0.0 && alpha <= 1.0) || !(c2 > 0.0))
     return fail(AAO_EINVAL, "bad tau/alpha/c2");
   AAO_CK(cudaSetDevice(h->device));
-  return set_params(h, tau, alpha, c2, h->cap_stream ? h->cap_stream : (cudaStream_t)0);
+  return set_params(h, tau, alpha, c2, h->own_stream);
 }
 
 // Enqueue one complete FP64 solve (DST of b, the graph-captured MINRES, DST back,
@@ -847,6 +897,128 @@ aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double 
   AAO_CK(launch_relres(p1, nb, p2, dot_blocks_per_rhs(h->P), h->relres_dev, 1, s, &h->launches));
   AAO_CK(cudaMemcpyAsync(h->relres_host, h->relres_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
   return AAO_OK;
+}
+
+// ---- grouped serving (aao_serve.cu): one problem per handle, iterations run by grouped launches ----
+aao_status aaoi_serving_prepare(aao_handle* h) {
+  if (!h) return fail(AAO_EINVAL, "null handle");
+  if (h->pin) return AAO_OK;
+  const Plan& P = h->P;
+  const size_t nt = (size_t)P.n;
+  const size_t bytes = 2 * nt * sizeof(double2) + 2 * nt * sizeof(double) + (size_t)P.m * sizeof(double) +
+                       2 * nt * sizeof(dfl) + (size_t)2 * h->mm_blocks * sizeof(double) + 64;
+  AAO_CK(cudaSetDevice(h->device));
+  AAO_CK(cudaMallocHost(&h->pin, bytes));
+  char* q = static_cast<char*>(h->pin);
+  auto carve = [&](size_t b) { char* r = q; q += (b + 15) & ~size_t(15); return r; };
+  h->pin_wq = reinterpret_cast<double2*>(carve(2 * nt * sizeof(double2)));
+  h->pin_dinv = reinterpret_cast<double*>(carve(nt * sizeof(double)));
+  h->pin_d2 = reinterpret_cast<double*>(carve(nt * sizeof(double)));
+  h->pin_dinv_ff = reinterpret_cast<dfl*>(carve(nt * sizeof(dfl)));
+  h->pin_d2_ff = reinterpret_cast<dfl*>(carve(nt * sizeof(dfl)));
+  h->pin_mm = reinterpret_cast<double*>(carve((size_t)2 * h->mm_blocks * sizeof(double)));
+  h->pin_lam = reinterpret_cast<double*>(carve((size_t)P.m * sizeof(double)));
+  return AAO_OK;
+}
+
+// Re-bind to (tau, alpha, c2) stream-ordered on s with no host synchronisation: host
+// tables into the pinned staging, then bind_tables; the |Sigma| check waits for
+// aaoi_group_collect.  The caller guarantees the staging is no longer in use (the
+// handle's previous solve has completed).
+aao_status aaoi_rebind_async(aao_handle* h, double tau, double alpha, double c2, cudaStream_t s) {
+  if (!h || !h->pin) return fail(AAO_EINVAL, "handle not prepared for serving");
+  if (!(tau > 0.0) || !(alpha > 0.0 && alpha <= 1.0) || !(c2 > 0.0)) return fail(AAO_EINVAL, "bad tau/alpha/c2");
+  if (h->precision != AAO_PREC_FP64 && h->precision != AAO_PREC_F32X2)
+    return fail(AAO_EINVAL, "served precision must be FP64 or double-float");
+  Plan& P = h->P;
+  param_tables(P, tau, alpha, c2, h->pin_wq, h->pin_dinv, h->pin_d2, h->pin_lam);
+  if (h->precision == AAO_PREC_F32X2)
+    for (int t = 0; t < P.n; ++t) {
+      h->pin_dinv_ff[t] = dfl(h->pin_dinv[t]);
+      h->pin_d2_ff[t] = dfl(h->pin_d2[t]);
+    }
+  return bind_tables(h, h->pin_wq, h->pin_dinv, h->pin_d2, h->pin_lam, nullptr, nullptr, h->pin_dinv_ff,
+                     h->pin_d2_ff, h->pin_mm, &h->pin_nb, s);
+}
+
+// b = Y f, b^ = (I (x) U) b and the MINRES initialisation from a zero guess (no graph),
+// stream-ordered on s; afterwards iteration j runs on the buffers of parity j & 1.
+aao_status aaoi_group_begin(aao_handle* h, const double* f, const double* psi0, const double* psi1, double* b,
+                            double rtol, int maxit, cudaStream_t s) {
+  if (!h || !f || !psi0 || !psi1 || !b) return fail(AAO_EINVAL, "null pointer");
+  AAO_KL(h, KC_RHS, s, launch_rhs(h, f, psi0, psi1, b, 1, s));
+  AAO_TRY(dst_apply(h, b, h->vbh, 1, s));
+  MinresCtx c{h, h->vbh, h->vxh, 1, rtol, maxit, s, true, false};
+  const MinresBufs B0{h->vv, h->vvp, h->vz, h->vzn, h->vw, h->vwp};
+  return minres_enqueue_init(c, 0, B0);
+}
+
+static MinresBufs group_bufs(aao_handle* h, int parity) {
+  const MinresBufs B0{h->vv, h->vvp, h->vz, h->vzn, h->vw, h->vwp};
+  return parity ? rotate(B0) : B0;
+}
+
+void aaoi_group_problem(aao_handle* h, int parity, GroupProblem* gp) {
+  const Plan& P = h->P;
+  const MinresBufs B = group_bufs(h, parity);
+  gp->z = B.z; gp->T = h->vT; gp->v = B.v; gp->vp = B.vp; gp->zn = B.zn; gp->w = B.w; gp->wp = B.wp;
+  gp->x = h->vxh; gp->b = h->vbh; gp->lam = h->lam64; gp->sc = h->sc; gp->partial = h->partial;
+  gp->n = P.n; gp->m = P.m;
+  gp->yt_gx = group_yt_tiles(P.m);
+  gp->nb_dot = dot_blocks_per_rhs(P);
+  gp->nb_vu = group_vu_blocks(P.n, P.m);
+}
+
+int aaoi_precision(const aao_handle* h) { return h->precision; }
+int aaoi_nt(const aao_handle* h) { return h->P.n; }
+int aaoi_modes(const aao_handle* h) { return h->P.m; }
+int aaoi_time_variant(const aao_handle* h) {
+  return h->precision == AAO_PREC_F32X2 ? h->P.time_variant_ff : h->P.time_variant64;
+}
+
+void aaoi_time_entry64(aao_handle* h, int parity, TimeGroupEntry<double>* e) {
+  const MinresBufs B = group_bufs(h, parity);
+  e->in = B.vp; e->out = B.zn; e->sc = h->sc; e->m = h->P.m; e->npairs = h->P.npairs; e->tb = h->P.t64;
+}
+void aaoi_time_entry_ff(aao_handle* h, int parity, TimeGroupEntry<dfl>* e) {
+  const MinresBufs B = group_bufs(h, parity);
+  e->in = B.vp; e->out = B.zn; e->sc = h->sc; e->m = h->P.m; e->npairs = h->P.npairs; e->tb = h->P.tff;
+}
+
+// the time step of iteration `parity` as a solo launch (variants without a grouped form)
+aao_status aaoi_group_time_solo(aao_handle* h, int parity, cudaStream_t s) {
+  const MinresBufs B = group_bufs(h, parity);
+  return time_apply(h, B.vp, B.zn, 1, s);
+}
+
+// x = (I (x) U) x^, the physical residual ||b - Y T x|| / ||b|| and the copies of the
+// scalars and the residual to the handle's pinned mirrors, stream-ordered on s
+aao_status aaoi_group_end(aao_handle* h, const double* b, double* x, cudaStream_t s) {
+  AAO_TRY(dst_apply(h, h->vxh, x, 1, s));
+  double* p1 = h->partial;
+  double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
+  int nb = 0;
+  AAO_CK(launch_op(h, x, nullptr, b, p1, 2, 1, s, &nb));
+  AAO_CK(launch_dot(h->P, b, b, p2, 1, s, &h->launches));
+  AAO_CK(launch_relres(p1, nb, p2, dot_blocks_per_rhs(h->P), h->relres_dev, 1, s, &h->launches));
+  AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(MinresScalars), cudaMemcpyDeviceToHost, s));
+  AAO_CK(cudaMemcpyAsync(h->relres_host, h->relres_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return AAO_OK;
+}
+
+// after the stream passed aaoi_group_end: the request's result
+aao_status aaoi_group_collect(aao_handle* h, double rtol, aao_solve_info* info) {
+  aao_status st = minres_collect(h, 1, info);
+  info->relres_true = h->relres_host[0];
+  if (info->relres_true > rtol && info->status == AAO_OK) info->status = AAO_ENOTCONV;
+  if (h->pin_nb > 0) {
+    const aao_status sg = check_sigma(h->pin_mm, h->pin_nb);
+    h->pin_nb = 0;
+    if (sg != AAO_OK) info->status = sg;
+  }
+  if (info->status != AAO_OK && st == AAO_OK) st = (aao_status)info->status;
+  if (info->status != AAO_OK) st = (aao_status)info->status;
+  return st;
 }
 
 aao_status aaoi_solve_collect(aao_handle* h, double rtol, aao_solve_info* info) {
@@ -913,11 +1085,17 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   if (o.nrhs_max < 1) o.nrhs_max = 1;
   if (o.precision != AAO_PREC_FP64 && o.precision != AAO_PREC_FP32_IR && o.precision != AAO_PREC_F32X2)
     return fail(AAO_EINVAL, "unknown precision");
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i] != 0) return fail(AAO_EINVAL, "opts.reserved must be zero");
 
   aao_handle* h = new aao_handle();
   cudaGetDevice(&h->device);
+  if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->own_stream = nullptr;
+    delete h;
+    return fail(AAO_ECUDA, "cudaStreamCreate failed");
+  }
   h->precision = o.precision;
   h->nrhs_max = o.nrhs_max;
   Plan& P = h->P;
@@ -1013,9 +1191,11 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     for (int i = 1; i < P.d; ++i) fsz *= P.N;
     if ((st = h->alloc(&h->face, fsz))) return bail(st);
   }
-  if (fp32) {
-    if ((st = h->alloc(&h->vr, vl)) || (st = h->alloc(&h->vdx, vl))) return bail(st);
+  if (fp32) {  // refinement vectors and the FP32 buffer of aao_apply_prec
+    if ((st = h->alloc(&h->vr, vl)) || (st = h->alloc(&h->vdx, vl)) || (st = h->alloc(&h->f32, vl)))
+      return bail(st);
   }
+  if (o.host_staging && (st = reserve_host_staging(h))) return bail(st);
   h->partial_stride = std::max(std::max(yt_blocks_per_rhs(P), dot_blocks_per_rhs(P)), wxres_blocks_per_rhs(P));
   if ((st = h->alloc(&h->partial, (size_t)3 * h->nrhs_max * h->partial_stride)) ||
       (st = h->alloc(&h->sc, (size_t)h->nrhs_max)))
@@ -1027,14 +1207,15 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   }
 
   auto run = [&]() -> aao_status {
-    AAO_TRY(upload(twS, h->tw_space64));
-    AAO_TRY(upload(sinw, h->sinw64));
-    AAO_TRY(upload(twT, h->tw_time64));
-    AAO_TRY(upload(mu, h->d_mu));
+    const cudaStream_t os = h->own_stream;
+    AAO_TRY(upload_on(twS, h->tw_space64, os));
+    AAO_TRY(upload_on(sinw, h->sinw64, os));
+    AAO_TRY(upload_on(twT, h->tw_time64, os));
+    AAO_TRY(upload_on(mu, h->d_mu, os));
     if (fp32) {
-      AAO_TRY(upload(to_f2(twS), h->tw_space32));
-      AAO_TRY(upload(to_f(sinw), h->sinw32));
-      AAO_TRY(upload(to_f2(twT), h->tw_time32));
+      AAO_TRY(upload_on(to_f2(twS), h->tw_space32, os));
+      AAO_TRY(upload_on(to_f(sinw), h->sinw32, os));
+      AAO_TRY(upload_on(to_f2(twT), h->tw_time32, os));
     }
     P.t64.tw_space = h->tw_space64; P.t64.sinw = h->sinw64; P.t64.tw_time = h->tw_time64;
     P.t64.dinv = h->dinv64; P.t64.d2 = h->d264; P.t64.ab = h->ab64;
@@ -1045,17 +1226,17 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
       P.t32.cq = (float)(cM / 4.0L);
     }
     if (ff_dst) {
-      AAO_TRY(upload(to_df2(twS), h->tw_space_ff));
-      AAO_TRY(upload(to_df(sinw), h->sinw_ff));
+      AAO_TRY(upload_on(to_df2(twS), h->tw_space_ff, os));
+      AAO_TRY(upload_on(to_df(sinw), h->sinw_ff, os));
       P.tff.tw_space = h->tw_space_ff; P.tff.sinw = h->sinw_ff;
       P.tff.cq = dfl((double)(cM / 4.0L));
     }
     if (ff) {
-      AAO_TRY(upload(to_df2(twT), h->tw_time_ff));
+      AAO_TRY(upload_on(to_df2(twT), h->tw_time_ff, os));
       P.tff.tw_time = h->tw_time_ff; P.tff.dinv = h->dinv_ff; P.tff.d2 = h->d2_ff; P.tff.ab = h->ab_ff;
     }
-    AAO_TRY(set_params(h, tau, alpha, grid->c2, 0));
-    AAO_CK(cudaDeviceSynchronize());
+    AAO_TRY(set_params(h, tau, alpha, grid->c2, os));
+    AAO_CK(cudaStreamSynchronize(os));  // this handle's work only, not the whole device
     return AAO_OK;
   };
   st = run();
@@ -1289,13 +1470,7 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
   AAO_TRY(check_call(h, nrhs));
   if (!f || !psi0 || !psi1 || !u) return fail(AAO_EINVAL, "null pointer");
   const Plan& P = h->P;
-  const size_t vl = (size_t)h->nrhs_max * h->vlen();
-  if (!h->hs_f) {
-    AAO_TRY(h->alloc(&h->hs_f, vl));
-    AAO_TRY(h->alloc(&h->hs_b, vl));
-    AAO_TRY(h->alloc(&h->hs_x, vl));
-    AAO_TRY(h->alloc(&h->hs_psi, (size_t)2 * h->nrhs_max * P.m));
-  }
+  if (!h->hs_f) AAO_TRY(reserve_host_staging(h));  // handles created without opts.host_staging
   cudaStream_t s = (cudaStream_t)stream;
   const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
   const size_t pb = (size_t)nrhs * P.m * sizeof(double);
@@ -1318,15 +1493,9 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
   // chunks already there, and the download of x overlaps the inverse DSTs of later
   // chunks.  Every level of the right-hand side and of the DSTs depends on its own f
   // level (and psi0, psi1) only, so chunking changes no value.
-  const int CH = 32;  // n is a power of two >= 64
+  const int CH = HOST_CHUNK;
   const int per = P.n / CH, nch = nrhs * per;
   const size_t lb = (size_t)P.m * sizeof(double);
-  if (!h->hs_copy) AAO_CK(cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking));
-  while ((int)h->hs_ev.size() < 2 * nch + 2) {
-    cudaEvent_t e = nullptr;
-    AAO_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    h->hs_ev.push_back(e);
-  }
   cudaStream_t cs = h->hs_copy;
   cudaEvent_t* ev = h->hs_ev.data();
   AAO_CK(cudaEventRecord(ev[2 * nch], s));  // the copy stream follows the caller's stream

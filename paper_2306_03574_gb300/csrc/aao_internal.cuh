@@ -182,6 +182,93 @@ cudaError_t launch_uncast(const float* in, double* out, size_t count, cudaStream
 cudaError_t launch_axpy(double a, const double* x, double* y, size_t count, cudaStream_t s,
                         uint64_t* nl);
 
+int dot_blocks_for(long long len);
+
+// ---------------------------------------------------------------------------
+// Grouped launches (serving): one launch performs the same MINRES step for up to
+// GROUP_MAX independent problems of different sizes.  Problem r owns blocks
+// [start[r], start[r+1]) of the launch (exclusive prefix sums of the problems' block
+// counts); each block finds its problem by binary search and runs the same device
+// code, on the same block decomposition, as the problem's solo launch, so a problem's
+// results are bit for bit those of its solo solve.  Problems whose scalars say done
+// are skipped.
+// ---------------------------------------------------------------------------
+constexpr int GROUP_MAX = 64;
+
+struct GroupProblem {
+  const double* z;   // z~_j (preconditioned Lanczos vector of this iteration)
+  double* T;         // Y T^ z~_j (operator output)
+  const double* v;   // v_j
+  double* vp;        // v_{j-1} in, v_{j+1} out
+  double* zn;        // z~_{j+1} (time-kernel output)
+  const double* w;   // w_j
+  double* wp;        // w_{j-1} in, w_{j+1} out
+  double* x;         // iterate (DST basis)
+  const double* b;   // right-hand side (DST basis)
+  const double* lam; // Lambda_s
+  MinresScalars* sc;
+  double* partial;   // the problem's partial-sum slots
+  int n, m;
+  int yt_gx;         // spatial tiles of the operator (its blocks: yt_gx x ceil(n/32))
+  int nb_dot;        // blocks of the dot product
+  int nb_vu;         // blocks of the v update
+};
+
+struct GroupRound {
+  int count;
+  int* flags;        // device, count entries: done flag of each problem after the round
+  int yt[GROUP_MAX + 1], dot[GROUP_MAX + 1], vu[GROUP_MAX + 1], wx[GROUP_MAX + 1];
+  GroupProblem p[GROUP_MAX];
+};
+
+// Time-pipeline launch over the problems of one (precision, n) bucket.
+template <typename R>
+struct TimeGroupEntry {
+  const double* in;
+  double* out;
+  const MinresScalars* sc;
+  int m, npairs;
+  PrecTables<R> tb;
+};
+template <typename R>
+struct TimeGroup {
+  int count;
+  int tile[GROUP_MAX + 1];
+  TimeGroupEntry<R> e[GROUP_MAX];
+};
+
+// the problem owning block b: the last r with start[r] <= b (start[0] = 0, count >= 1)
+__device__ __forceinline__ int group_find(const int* __restrict__ start, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// blocks of each grouped launch for one problem of n time levels and m modes
+int group_yt_tiles(int m);
+int group_yt_blocks(int n, int m);
+int group_wx_blocks(int m);
+int group_vu_blocks(int n, int m);
+// time-kernel tiles of a problem with m modes for time length L and variant v
+int time_tiles(int L, int variant, int m);
+
+// The grouped launches of one MINRES iteration (d_round: device copy of the round's
+// descriptors; totals: the launch's block counts from the host copy).
+cudaError_t launch_group_ythat(const GroupRound* d_round, int total_blocks, cudaStream_t s);
+cudaError_t launch_group_scalars(int step, const GroupRound* d_round, int count, cudaStream_t s);
+cudaError_t launch_group_vupdate(const GroupRound* d_round, int total_blocks, cudaStream_t s);
+cudaError_t launch_group_dot(const GroupRound* d_round, int total_blocks, cudaStream_t s);
+cudaError_t launch_group_wx_res(const GroupRound* d_round, int total_blocks, cudaStream_t s);
+// the time-kernel variant that has a grouped form (the default one of the precision)
+template <typename R>
+int group_time_variant();
+template <typename R>
+cudaError_t launch_group_time(int L, int variant, const TimeGroup<R>* d_group, int total_tiles, cudaStream_t s);
+
 }  // namespace aao
 
 // Handle-level internals used by the serving runtime (defined in aao_api.cu).
@@ -190,3 +277,19 @@ aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double 
                               cudaStream_t s);
 aao_status aaoi_solve_collect(aao_handle* h, double rtol, aao_solve_info* info);
 size_t aaoi_estimate_bytes(int dim, int N, int nt, int precision);
+// Grouped serving: a handle carries one problem whose MINRES iterations are run by the
+// grouped launches (GroupRound); see aao_api.cu for the contract of each call.
+aao_status aaoi_serving_prepare(aao_handle* h);
+aao_status aaoi_rebind_async(aao_handle* h, double tau, double alpha, double c2, cudaStream_t s);
+aao_status aaoi_group_begin(aao_handle* h, const double* f, const double* psi0, const double* psi1, double* b,
+                            double rtol, int maxit, cudaStream_t s);
+void aaoi_group_problem(aao_handle* h, int parity, aao::GroupProblem* gp);
+int aaoi_precision(const aao_handle* h);
+int aaoi_nt(const aao_handle* h);
+int aaoi_modes(const aao_handle* h);
+int aaoi_time_variant(const aao_handle* h);
+void aaoi_time_entry64(aao_handle* h, int parity, aao::TimeGroupEntry<double>* e);
+void aaoi_time_entry_ff(aao_handle* h, int parity, aao::TimeGroupEntry<aao::dfl>* e);
+aao_status aaoi_group_time_solo(aao_handle* h, int parity, cudaStream_t s);
+aao_status aaoi_group_end(aao_handle* h, const double* b, double* x, cudaStream_t s);
+aao_status aaoi_group_collect(aao_handle* h, double rtol, aao_solve_info* info);

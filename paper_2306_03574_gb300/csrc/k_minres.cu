@@ -19,7 +19,8 @@ namespace aao {
 
 namespace {
 constexpr int VNT = 256;
-constexpr int DOT_BLOCKS = 608;  // partial sums per right-hand side (4 per SM)
+constexpr int DOT_BLOCKS = 608;  // most partial sums per right-hand side (4 per SM)
+constexpr int DOT_PER_BLOCK = 4 * VNT;  // fewest elements per block: small vectors take fewer blocks
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -27,13 +28,14 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(VNT) k_dot(const double* __restrict__ a, const double* __restrict__ c,
-                                             double* __restrict__ partial, long long len) {
-  const long long rb = (long long)blockIdx.y * len;
+// Block bx of nbx blocks: the partial sum of a_i c_i over i = bx*VNT + t + k*nbx*VNT
+// (fixed assignment, so the partials do not depend on anything but nbx).
+__device__ __forceinline__ void dot_body(const double* __restrict__ a, const double* __restrict__ c,
+                                         double* __restrict__ out, long long len, int bx, int nbx) {
   double acc = 0.0;
 #pragma unroll 4
-  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT)
-    acc = fma(a[rb + i], c[rb + i], acc);
+  for (long long i = (long long)bx * VNT + threadIdx.x; i < len; i += (long long)nbx * VNT)
+    acc = fma(a[i], c[i], acc);
   __shared__ double red[VNT / 32];
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -41,22 +43,31 @@ __global__ void __launch_bounds__(VNT) k_dot(const double* __restrict__ a, const
   if (threadIdx.x < 32) {
     double t = (threadIdx.x < VNT / 32) ? red[threadIdx.x] : 0.0;
     t = warp_sum(t);
-    if (threadIdx.x == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    if (threadIdx.x == 0) *out = t;
   }
+}
+
+__global__ void __launch_bounds__(VNT) k_dot(const double* __restrict__ a, const double* __restrict__ c,
+                                             double* __restrict__ partial, long long len) {
+  const long long rb = (long long)blockIdx.y * len;
+  dot_body(a + rb, c + rb, partial + (long long)blockIdx.y * gridDim.x + blockIdx.x, len, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void vupdate_body(const double* __restrict__ T, const double* __restrict__ v,
+                                             double* __restrict__ vprev, const MinresScalars& S, long long len,
+                                             int bx, int nbx) {
+  const bool dn = S.done != 0;
+  const double c0 = S.cv[0], c1 = S.cv[1], c2 = S.cv[2];
+#pragma unroll 4
+  for (long long k = (long long)bx * VNT + threadIdx.x; k < len; k += (long long)nbx * VNT)
+    vprev[k] = dn ? 0.0 : fma(c0, T[k], fma(c1, v[k], c2 * vprev[k]));
 }
 
 __global__ void __launch_bounds__(VNT) k_vupdate(const double* __restrict__ T, const double* __restrict__ v,
                                                  double* __restrict__ vprev, const MinresScalars* __restrict__ sc,
                                                  long long len) {
-  const MinresScalars& S = sc[blockIdx.y];
   const long long rb = (long long)blockIdx.y * len;
-  const bool dn = S.done != 0;
-  const double c0 = S.cv[0], c1 = S.cv[1], c2 = S.cv[2];
-#pragma unroll 4
-  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT) {
-    const long long k = rb + i;
-    vprev[k] = dn ? 0.0 : fma(c0, T[k], fma(c1, v[k], c2 * vprev[k]));
-  }
+  vupdate_body(T + rb, v + rb, vprev + rb, sc[blockIdx.y], len, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(VNT) k_wxupdate(const double* __restrict__ z, double* __restrict__ wprev,
@@ -117,16 +128,17 @@ __device__ __forceinline__ double sum_partials(const double* p, int nb) {
   return warp_sum(((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7])));
 }
 
-__global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict__ p1, int nb1,
-                          const double* __restrict__ p2, int nb2, const double* __restrict__ p3,
-                          int nb3, double rtol, int maxit, const double* __restrict__ prm) {
-  const int r = blockIdx.x;
-  MinresScalars& S = sc[r];
-  const double s1 = sum_partials(p1 + (long long)r * nb1, nb1);
+// One warp: the scalar step of one right-hand side from its partial sums p1 (and, at
+// step 0, p2 and p3), in a fixed order.
+__device__ __forceinline__ void scalars_body(int step, MinresScalars& S, const double* __restrict__ p1,
+                                             int nb1, const double* __restrict__ p2, int nb2,
+                                             const double* __restrict__ p3, int nb3, double rtol, int maxit,
+                                             const double* __restrict__ prm) {
+  const double s1 = sum_partials(p1, nb1);
   double s2 = 0.0, s3 = 0.0;
   if (step == 0) {
-    s2 = sum_partials(p2 + (long long)r * nb2, nb2);
-    s3 = sum_partials(p3 + (long long)r * nb3, nb3);
+    s2 = sum_partials(p2, nb2);
+    s3 = sum_partials(p3, nb3);
   }
   if (threadIdx.x != 0) return;
   if (step == 0) {
@@ -146,7 +158,7 @@ __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict_
     for (int i = 0; i < 3; ++i) S.cv[i] = 0.0;
     for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
     if (s1 < 0.0) { S.status = AAO_EBREAKDOWN; S.done = 1; }
-    if (s1 == 0.0 || S.relres_true <= rtol) S.done = 1;
+    if (s1 == 0.0 || S.relres_true <= S.rtol) S.done = 1;
     S.gam = S.done ? 0.0 : sqrt(s1);
     S.gam1 = S.gam;
     S.eta = S.gam;
@@ -218,6 +230,14 @@ __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict_
   }
 }
 
+__global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict__ p1, int nb1,
+                          const double* __restrict__ p2, int nb2, const double* __restrict__ p3,
+                          int nb3, double rtol, int maxit, const double* __restrict__ prm) {
+  const int r = blockIdx.x;
+  scalars_body(step, sc[r], p1 + (long long)r * nb1, nb1, p2 + (long long)r * nb2, nb2,
+               p3 + (long long)r * nb3, nb3, rtol, maxit, prm);
+}
+
 // relres[r] = sqrt(sum r^2 / sum b^2) (absolute norm if b = 0)
 __global__ void k_relres(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2,
                          double* __restrict__ relres) {
@@ -242,6 +262,34 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle hw, const MinresScalars* 
   cudaGraphSetConditional(hw, (any && t < trip_limit) ? 1u : 0u);
 }
 
+// ---- grouped launches (serving): see GroupRound ----
+__global__ void __launch_bounds__(VNT) k_g_vupdate(const GroupRound* __restrict__ g) {
+  const int r = group_find(g->vu, g->count, blockIdx.x);
+  const GroupProblem& P = g->p[r];
+  if (P.sc->done) return;
+  vupdate_body(P.T, P.v, P.vp, *P.sc, (long long)P.n * P.m, blockIdx.x - g->vu[r], P.nb_vu);
+}
+
+// <z~_{j+1}, v_{j+1}> of every problem
+__global__ void __launch_bounds__(VNT) k_g_dot(const GroupRound* __restrict__ g) {
+  const int r = group_find(g->dot, g->count, blockIdx.x);
+  const GroupProblem& P = g->p[r];
+  if (P.sc->done) return;
+  const int lb = blockIdx.x - g->dot[r];
+  dot_body(P.zn, P.vp, P.partial + lb, (long long)P.n * P.m, lb, P.nb_dot);
+}
+
+// steps 1 (delta; the operator's partials), 2 (gamma + Givens; the dot's partials) and
+// 3 (true-residual stop test; the w/x update's partials), one warp per problem; step 3
+// also publishes each problem's done flag
+__global__ void k_g_scalars(int step, const GroupRound* __restrict__ g) {
+  const int r = blockIdx.x;
+  const GroupProblem& P = g->p[r];
+  const int nb = step == 1 ? g->yt[r + 1] - g->yt[r] : step == 2 ? P.nb_dot : g->wx[r + 1] - g->wx[r];
+  scalars_body(step, *P.sc, P.partial, nb, nullptr, 0, nullptr, 0, 0.0, 0, nullptr);
+  if (step == 3 && threadIdx.x == 0) g->flags[r] = P.sc->done;
+}
+
 inline dim3 vgrid(const Plan& P, int nrhs) {
   const long long len = (long long)P.n * P.m;
   long long b = (len + VNT - 1) / VNT;
@@ -251,12 +299,37 @@ inline dim3 vgrid(const Plan& P, int nrhs) {
 
 }  // namespace
 
-int dot_blocks_per_rhs(const Plan&) { return DOT_BLOCKS; }
+int dot_blocks_for(long long len) {
+  const long long b = (len + DOT_PER_BLOCK - 1) / DOT_PER_BLOCK;
+  return (int)(b < 1 ? 1 : (b > DOT_BLOCKS ? DOT_BLOCKS : b));
+}
+
+int dot_blocks_per_rhs(const Plan& P) { return dot_blocks_for((long long)P.n * P.m); }
+
+int group_vu_blocks(int n, int m) {
+  const long long b = ((long long)n * m + 4 * VNT - 1) / (4 * VNT);
+  return (int)(b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b));
+}
+
+cudaError_t launch_group_vupdate(const GroupRound* d_round, int total_blocks, cudaStream_t s) {
+  k_g_vupdate<<<total_blocks, VNT, 0, s>>>(d_round);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_dot(const GroupRound* d_round, int total_blocks, cudaStream_t s) {
+  k_g_dot<<<total_blocks, VNT, 0, s>>>(d_round);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_scalars(int step, const GroupRound* d_round, int count, cudaStream_t s) {
+  k_g_scalars<<<count, 32, 0, s>>>(step, d_round);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dot(const Plan& P, const double* a, const double* c, double* partial, int nrhs,
                        cudaStream_t s, uint64_t* nl) {
   if (nl) ++*nl;
-  k_dot<<<dim3(DOT_BLOCKS, nrhs), VNT, 0, s>>>(a, c, partial, (long long)P.n * P.m);
+  k_dot<<<dim3(dot_blocks_per_rhs(P), nrhs), VNT, 0, s>>>(a, c, partial, (long long)P.n * P.m);
   return cudaGetLastError();
 }
 

@@ -8,11 +8,17 @@
 // aao_residual_norm needs a handle, and creating a handle allocates; this entry
 // point needs neither.
 //
-// Its only scratch is the file-scope device array g_noalloc_scratch below: every
-// GPU that loads the library holds it (256 KiB) until the process exits.  Host
-// code cannot pass the array's name to a kernel (in host code the name is a host
-// stand-in, not a device address), so the device address is looked up once per
+// Its only scratch is the file-scope device array g_noalloc_scratch below (256 KiB).
+// Host code cannot pass the array's name to a kernel (in host code the name is a
+// host stand-in, not a device address), so the device address is looked up once per
 // device with cudaGetSymbolAddress, with that device current, on the first call.
+// With CUDA's lazy module loading (the default) that first lookup is also what loads
+// this file's module -- the array and the kernels -- onto the device: a driver-side
+// allocation of about 256 KiB plus code, held from then until the process exits (or
+// until the device is reset).  Callers that cannot allocate at all later on make the
+// first call at initialisation time; every call after it allocates nothing.  The
+// cached address does not survive cudaDeviceReset (the module is unloaded with the
+// context): a process that resets the device must not call this entry point again.
 #include <mutex>
 #include <string>
 

@@ -98,26 +98,25 @@ __global__ void __launch_bounds__(YT_NT) k_yt(const double* __restrict__ x, doub
 // (Y T^ v)_{n-1-i} = Lambda_s (v_i + v_{i-2}) - 2 v_{i-1} pointwise in s.  Modes as k_yt,
 // plus mode 3: the residual vector y = w - Y T^ v written out with the sum of its squares
 // (the refinement loop's r = b - A x and ||r||^2 in one pass).
+// Block (bx, by) of one right-hand side (x, y, w point at it): spatial tile bx, time run
+// by; its partial sum (modes 1-3) goes to *part.
 template <int MODE>
-__global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, double* __restrict__ y,
-                                                 const double* __restrict__ w,
-                                                 double* __restrict__ partial,
-                                                 const double* __restrict__ lam, YtArgs a) {
-  const int s = blockIdx.x * YT_NT + threadIdx.x;
-  const int n = a.n, m = a.m;
-  const int i0 = blockIdx.y * YT_CH;
+__device__ __forceinline__ void ythat_body(const double* __restrict__ x, double* __restrict__ y,
+                                           const double* __restrict__ w, double* __restrict__ part,
+                                           const double* __restrict__ lam, int n, int m, int bx, int by) {
+  const int s = bx * YT_NT + threadIdx.x;
+  const int i0 = by * YT_CH;
   const int i1 = min(n, i0 + YT_CH);
-  const long long rb = (long long)blockIdx.z * n * m;
   double acc = 0.0;
   if (s < m) {
     const double ls = lam[s];
-    const double* xr = x + rb + s;
+    const double* xr = x + s;
     double x1 = 0.0, x2 = 0.0;  // v_{i-1}, v_{i-2}
     for (int i = max(0, i0 - 2); i < i1; ++i) {
       const double xi = xr[(long long)i * m];
       if (i >= i0) {
         const double o = fma(-2.0, x1, ls * (xi + x2));
-        const long long idx = rb + (long long)(n - 1 - i) * m + s;
+        const long long idx = (long long)(n - 1 - i) * m + s;
         if (MODE == 0 || MODE == 1) y[idx] = o;
         if (MODE == 1) acc = fma(o, w[idx], acc);
         if (MODE >= 2) {
@@ -132,11 +131,20 @@ __global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, d
   }
   if (MODE != 0) {
     const double t = block_sum(acc);
-    if (threadIdx.x == 0) {
-      const long long nb = (long long)gridDim.x * gridDim.y;
-      partial[blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
-    }
+    if (threadIdx.x == 0) *part = t;
   }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, double* __restrict__ y,
+                                                 const double* __restrict__ w,
+                                                 double* __restrict__ partial,
+                                                 const double* __restrict__ lam, YtArgs a) {
+  const long long rb = (long long)blockIdx.z * a.n * a.m;
+  const long long nb = (long long)gridDim.x * gridDim.y;
+  double* part = MODE != 0 ? partial + blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x : nullptr;
+  ythat_body<MODE>(x + rb, y ? y + rb : nullptr, w ? w + rb : nullptr, part, lam, a.n, a.m, blockIdx.x,
+                   blockIdx.y);
 }
 
 // One MINRES step's direction and iterate update fused with the true residual, in the
@@ -154,19 +162,19 @@ constexpr int WXR_S = 32;
 constexpr int WXR_C = 4;
 constexpr int WXR_NT = WXR_S * WXR_C;
 
-__global__ void __launch_bounds__(WXR_NT) k_wx_res(const double* __restrict__ z, double* __restrict__ wprev,
-                                                   const double* __restrict__ w, double* __restrict__ x,
-                                                   const double* __restrict__ b, const double* __restrict__ lam,
-                                                   const MinresScalars* __restrict__ sc,
-                                                   double* __restrict__ partial, int n, int m) {
-  const MinresScalars& S = sc[blockIdx.y];
+// Block bx of one right-hand side (vectors point at it); partial sum to *part.
+__device__ __forceinline__ void wx_res_body(const double* __restrict__ z, double* __restrict__ wprev,
+                                            const double* __restrict__ w, double* __restrict__ x,
+                                            const double* __restrict__ b, const double* __restrict__ lam,
+                                            const MinresScalars& S, double* __restrict__ part, int n, int m,
+                                            int bx) {
   if (S.done) return;  // uniform over the block
-  const int s = blockIdx.x * WXR_S + (int)(threadIdx.x % WXR_S);
+  const int s = bx * WXR_S + (int)(threadIdx.x % WXR_S);
   const int len = n / WXR_C;
   const int i0 = (int)(threadIdx.x / WXR_S) * len;
   const bool on = s < m;
   const double c0 = S.cw[0], c1 = S.cw[1], c2 = S.cw[2], c3 = S.cw[3];
-  const long long rb = (long long)blockIdx.y * n * m + s;
+  const long long rb = s;
   const double* zp = z + rb;
   double* wpp = wprev + rb;
   const double* wq = w + rb;
@@ -196,7 +204,36 @@ __global__ void __launch_bounds__(WXR_NT) k_wx_res(const double* __restrict__ z,
     }
   }
   const double t = block_sum<WXR_NT>(acc);
-  if (threadIdx.x == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  if (threadIdx.x == 0) *part = t;
+}
+
+__global__ void __launch_bounds__(WXR_NT) k_wx_res(const double* __restrict__ z, double* __restrict__ wprev,
+                                                   const double* __restrict__ w, double* __restrict__ x,
+                                                   const double* __restrict__ b, const double* __restrict__ lam,
+                                                   const MinresScalars* __restrict__ sc,
+                                                   double* __restrict__ partial, int n, int m) {
+  const long long rb = (long long)blockIdx.y * n * m;
+  wx_res_body(z + rb, wprev + rb, w + rb, x + rb, b + rb, lam, sc[blockIdx.y],
+              partial + (long long)blockIdx.y * gridDim.x + blockIdx.x, n, m, blockIdx.x);
+}
+
+// ---- grouped launches (serving): see GroupRound ----
+// Y T^ z~_j and its partial dot with z~_j (mode 1) for every problem
+__global__ void __launch_bounds__(YT_NT) k_g_ythat(const GroupRound* __restrict__ g) {
+  const int r = group_find(g->yt, g->count, blockIdx.x);
+  const GroupProblem& P = g->p[r];
+  if (P.sc->done) return;
+  const int lb = blockIdx.x - g->yt[r];
+  const int bx = lb % P.yt_gx, by = lb / P.yt_gx;
+  ythat_body<1>(P.z, P.T, P.z, P.partial + lb, P.lam, P.n, P.m, bx, by);
+}
+
+// the w/x update fused with the true residual for every problem
+__global__ void __launch_bounds__(WXR_NT) k_g_wx_res(const GroupRound* __restrict__ g) {
+  const int r = group_find(g->wx, g->count, blockIdx.x);
+  const GroupProblem& P = g->p[r];
+  const int lb = blockIdx.x - g->wx[r];
+  wx_res_body(P.z, P.wp, P.w, P.x, P.b, P.lam, *P.sc, P.partial + lb, P.n, P.m, lb);
 }
 
 // Variable coefficient: L_a w(s) = w(s) + cv sum_axes [aR (w(s) - w(s+e)) + aL (w(s) - w(s-e))],
@@ -350,6 +387,20 @@ YtArgs make_args(const Plan& P) {
 }  // namespace
 
 int wxres_blocks_per_rhs(const Plan& P) { return (P.m + WXR_S - 1) / WXR_S; }
+
+int group_yt_tiles(int m) { return (m + YT_NT - 1) / YT_NT; }
+int group_yt_blocks(int n, int m) { return group_yt_tiles(m) * ((n + YT_CH - 1) / YT_CH); }
+int group_wx_blocks(int m) { return (m + WXR_S - 1) / WXR_S; }
+
+cudaError_t launch_group_ythat(const GroupRound* d_round, int total_blocks, cudaStream_t s) {
+  k_g_ythat<<<total_blocks, YT_NT, 0, s>>>(d_round);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_wx_res(const GroupRound* d_round, int total_blocks, cudaStream_t s) {
+  k_g_wx_res<<<total_blocks, WXR_NT, 0, s>>>(d_round);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_wx_res(const Plan& P, const double* lam, const double* z, double* wprev_out,
                           const double* w, double* x, const double* b, const MinresScalars* sc,

@@ -130,8 +130,10 @@ template <typename R, int L> struct FoldScaling { static constexpr bool value = 
 template <int L> struct FoldScaling<double, L> { static constexpr bool value = true; };
 template <int L> struct FoldScaling<float, L> { static constexpr bool value = L <= 256; };
 
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1>
-__global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
+// Tile `tile` (mode pairs tile*NS ..) of one right-hand side: in and out point at it.
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG>
+__device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArgs& a, const PrecTables<R>& tb,
+                                          int tile) {
   using C = typename Cplx<R>::T;
   using Y = SLay<L, NS, LAY>;
   constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
@@ -145,9 +147,8 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
 
   const int tid = threadIdx.x;
   const int m = a.m;
-  const int s0 = blockIdx.x * (2 * NS);
-  const int p0 = blockIdx.x * NS;
-  const long long rb = (long long)blockIdx.y * L * m;
+  const int s0 = tile * (2 * NS);
+  const int p0 = tile * NS;
   if constexpr (STAGED) stage_table<L, NS, NT>(tab, tb.ab, a.npairs, p0);
   for (int i = tid; i < L; i += NT) {
     tw[i] = tb.tw_time[i];
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
     const int sa = s0 + 2 * q;
-    const TIO* p = in + rb + (long long)t * m + sa;
+    const TIO* p = in + (long long)t * m + sa;
     const R di = FOLD ? R(1) : dinv[t];
     C z;
     z.x = (sa < m) ? (FOLD ? R(p[0]) : R(p[0]) * di) : R();
@@ -195,12 +196,18 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
   for (int task = tid; task < NS * L; task += NT) {
     const int q = task % NS, t = task / NS;
     const int sa = s0 + 2 * q;
-    TIO* p = out + rb + (long long)t * m + sa;
+    TIO* p = out + (long long)t * m + sa;
     const C z = cbuf[Y::at(q, t)];
     const R di = dinv[t];
     if (sa < m) p[0] = TIO(z.x * di);
     if (sa + 1 < m) p[1] = TIO(z.y * di);
   }
+}
+
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1>
+__global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
+  const long long rb = (long long)blockIdx.y * L * a.m;
+  time_body<R, TIO, L, NS, NT, FFTV, LAY, STG>(in + rb, out + rb, a, tb, blockIdx.x);
 }
 
 // Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.

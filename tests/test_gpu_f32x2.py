@@ -9,6 +9,8 @@ import os
 import numpy as np
 import pytest
 
+import gates
+import guards
 import workloads as W
 from oracle import fast as OF
 from oracle import system as OS
@@ -17,8 +19,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2306_03574_gb300 as aao  # noqa: E402
-
-U_DW = 2.0 ** -47  # unit round-off of the double-word operations used (a few ulps of 2^-48)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -42,12 +42,6 @@ def relerr(a, b):
     return e
 
 
-def dw_tol(alpha, n):
-    # round-off of the transforms (~u log2 n per pass) amplified by D_alpha^{-1}, at most
-    # alpha^{-(n-1)/n}; the same form as the FP32 gate with the double-word unit
-    return 64 * U_DW * np.log2(n) * alpha ** (-(n - 1) / n)
-
-
 @pytest.mark.parametrize("d,N,nt", [(1, 255, 256), (2, 63, 64), (2, 127, 128), (3, 63, 64)])
 @pytest.mark.parametrize("alpha", [1e-1, 1e-3, 1e-6])
 def test_f32x2_prec_parity(d, N, nt, alpha):
@@ -56,13 +50,14 @@ def test_f32x2_prec_parity(d, N, nt, alpha):
     ref = OF.ABACPreconditioner(d, N, nt, tau, alpha).apply(x)
     with aao.Solver(d, N, nt, tau, alpha, precision=aao.AAO_PREC_F32X2) as s:
         xt = cu(x)
-        zt = torch.empty_like(xt)
+        zt = guards.guarded_empty(xt.shape)
         s.apply_prec(xt, zt)
         torch.cuda.synchronize()
         err = relerr(zt.cpu().numpy(), ref)
-    assert err < dw_tol(alpha, nt), err
+        guards.check(zt)
+    assert err < gates.dword("prec", d, N, nt, alpha), err
     # far more accurate than FP32: at least 1e4 times below the FP32 gate
-    assert err < 1e-4 * 64 * 2.0 ** -24 * np.log2(nt) * alpha ** (-(nt - 1) / nt)
+    assert err < 1e-4 * gates.fp32("prec", d, N, nt, alpha)
 
 
 @pytest.mark.parametrize("d,N,nt", [(2, 63, 64), (1, 511, 512), (1, 255, 1024)])
@@ -79,7 +74,7 @@ def test_f32x2_time_variants(d, N, nt, monkeypatch):
             yt = torch.empty_like(xt)
             s.apply_time(xt, yt)
             torch.cuda.synchronize()
-            assert relerr(yt.cpu().numpy(), ref) < dw_tol(alpha, nt), v
+            assert relerr(yt.cpu().numpy(), ref) < gates.dword("time", d, N, nt, alpha), v
 
 
 @pytest.mark.parametrize("N,nt", [(63, 64), (127, 128), (255, 256)])
@@ -153,7 +148,7 @@ def test_f32x2_dst_parity(d, N, monkeypatch):
             yt = torch.empty_like(xt)
             s.apply_dst(xt, yt)
             torch.cuda.synchronize()
-            assert relerr(yt.cpu().numpy(), ref) < 64 * U_DW * np.log2(N + 1) * d, dv
+            assert relerr(yt.cpu().numpy(), ref) < gates.dword("dst", d, N, nt), dv
 
 
 @pytest.mark.parametrize("scale", [1e-25, 1e-3, 1.0, 1e30])
@@ -172,9 +167,9 @@ def test_f32x2_conversions_across_scales(scale):
         s.apply_dst(xt, yt)
         torch.cuda.synchronize()
         y = yt.cpu().numpy()
-        assert relerr(y, ref) < 64 * U_DW * np.log2(N + 1) * d
+        assert relerr(y, ref) < gates.dword("dst", d, N, nt)
         assert np.all(y[5] == 0.0)
         # U is an involution: applying it again returns x to the same accuracy
         s.apply_dst(yt, yt)
         torch.cuda.synchronize()
-        assert relerr(yt.cpu().numpy(), x) < 2 * 64 * U_DW * np.log2(N + 1) * d
+        assert relerr(yt.cpu().numpy(), x) < 2 * gates.dword("dst", d, N, nt)

@@ -5,6 +5,8 @@ import os
 import numpy as np
 import pytest
 
+import gates
+import guards
 import workloads as W
 from oracle import fast as OF
 from oracle import minres as OM
@@ -41,11 +43,6 @@ def relerr(a, b):
     return e
 
 
-def prec_tol(alpha):
-    # FP64 round-off of the alpha-scaled FFT pipeline grows like eps/alpha
-    return 1e-12 if alpha >= 1e-3 else 1e-9
-
-
 SIZES = [  # (d, N, nt, nrhs): several tiles, ragged tails (N odd, m odd), batches
     (1, 63, 64, 1), (1, 127, 128, 3), (1, 511, 1024, 1), (1, 255, 512, 2),
     (2, 63, 64, 1), (2, 127, 128, 1), (2, 63, 256, 2), (2, 255, 64, 1),
@@ -61,7 +58,7 @@ def test_dst_parity(d, N, nt, nrhs):
     ref = np.stack([OF.apply_space(x[r], S, d, N) for r in range(nrhs)])
     with aao.Solver(d, N, nt, 1.0 / nt, 0.1, nrhs_max=nrhs) as s:
         xt = cu(x)
-        yt = torch.empty_like(xt)
+        yt = guards.guarded_empty(xt.shape)
         s.apply_dst(xt, yt)
         torch.cuda.synchronize()
         assert relerr(yt.cpu().numpy(), ref) < 1e-13
@@ -69,6 +66,7 @@ def test_dst_parity(d, N, nt, nrhs):
         s.apply_dst(yt, yt)
         torch.cuda.synchronize()
         assert relerr(yt.cpu().numpy(), x) < 1e-13
+        guards.check(yt)
 
 
 @pytest.mark.parametrize("d,N,nt,nrhs", SIZES[:8])
@@ -84,10 +82,11 @@ def test_time_pipeline_parity(d, N, nt, nrhs, alpha):
                     for r in range(nrhs)])
     with aao.Solver(d, N, nt, tau, alpha, nrhs_max=nrhs) as s:
         xt = cu(x)
-        yt = torch.empty_like(xt)
+        yt = guards.guarded_empty(xt.shape)
         s.apply_time(xt, yt)
         torch.cuda.synchronize()
-        assert relerr(yt.cpu().numpy(), ref) < prec_tol(alpha)
+        assert relerr(yt.cpu().numpy(), ref) < gates.fp64("time", d, N, nt, alpha)
+        guards.check(yt)
 
 
 @pytest.mark.parametrize("d,N,nt,nrhs", SIZES)
@@ -100,16 +99,18 @@ def test_prec_parity(d, N, nt, nrhs, alpha):
     pc = OF.ABACPreconditioner(d, N, nt, tau, alpha)
     ref = np.stack([pc.apply(x[r]) for r in range(nrhs)])
     with aao.Solver(d, N, nt, tau, alpha, nrhs_max=nrhs) as s:
-        xt = cu(x)
-        zt = torch.empty_like(xt)
+        xt = guards.guarded_copy(x)
+        zt = guards.guarded_empty(xt.shape)
         s.apply_prec(xt, zt)
         torch.cuda.synchronize()
         z = zt.cpu().numpy()
-        assert relerr(z, ref) < prec_tol(alpha)
+        assert relerr(z, ref) < gates.fp64("prec", d, N, nt, alpha)
+        guards.check(zt)
         # in place gives the same bits
         s.apply_prec(xt, xt)
         torch.cuda.synchronize()
         assert np.array_equal(xt.cpu().numpy(), z)
+        guards.check(xt)
 
 
 @pytest.mark.parametrize("d,N,nt,nrhs,c2", [(1, 63, 64, 1, 1.0), (2, 63, 64, 2, 1.0), (2, 255, 256, 1, 1.0),
@@ -124,15 +125,17 @@ def test_operator_and_rhs_parity(d, N, nt, nrhs, c2):
     p1 = W.random_field((nrhs, m), seed=403)
     with aao.Solver(d, N, nt, tau, 0.1, c2=c2, nrhs_max=nrhs) as s:
         xt = cu(x)
-        yt = torch.empty_like(xt)
+        yt = guards.guarded_empty(xt.shape)
         s.apply_op(xt, yt)
-        bt = torch.empty_like(xt)
+        bt = guards.guarded_empty(xt.shape)
         s.build_rhs(cu(f), cu(p0), cu(p1), bt)
         torch.cuda.synchronize()
         assert relerr(yt.cpu().numpy(), ref) < 1e-14
+        guards.check(yt)
         for r in range(nrhs):
             prob = W.WaveProblem(d, N, nt, 1.0, c2, 0.1, p0[r], p1[r], f[r])
             assert relerr(bt.cpu().numpy()[r], OS.rhs_b(prob)) < 1e-14
+        guards.check(bt)
 
 
 def _solve_both(p, rtol=1e-8, maxit=60):
@@ -185,7 +188,11 @@ def test_full_size_2d_prec_and_invariants():
     <P^{-1}x, y> = <x, P^{-1}y>; deterministic bits."""
     d, N, nt = 2, 255, 256
     tau = 1.0 / nt
-    for alpha, tol in ((1e-2, 1e-12), (1e-6, 1e-9)):
+    # P^{-1}: the error model at alpha = 1e-2; at alpha = 1e-6 the specification's 1e-9,
+    # since the max over 16.6 M entries sits above the small-case model there (measured
+    # 1.4e-10).  The invariants' gates sit within 30x of their measured values
+    # (Q^2 = I: 1.2e-13 and 6.0e-11).
+    for alpha, tol, tol_inv in ((1e-2, gates.fp64("prec", d, N, nt, 1e-2), 1e-12), (1e-6, 1e-9, 1e-9)):
         x = W.random_field((nt, N * N), seed=500)
         pc = OF.ABACPreconditioner(d, N, nt, tau, alpha)
         ref = pc.apply(x)
@@ -208,14 +215,15 @@ def test_full_size_2d_prec_and_invariants():
             q2 = torch.empty_like(xt)
             s.apply_prec(cu(yc2), q2)
             torch.cuda.synchronize()
-            assert relerr(q2.cpu().numpy(), x) < max(1e-12, 1e-13 / alpha)
+            assert relerr(q2.cpu().numpy(), x) < tol_inv
             y = W.random_field((nt, N * N), seed=501)
             py = torch.empty_like(xt)
             s.apply_prec(cu(y), py)
             torch.cuda.synchronize()
             a1 = float(np.vdot(z, y))
             a2 = float(np.vdot(x, py.cpu().numpy()))
-            assert abs(a1 - a2) / abs(a1) < max(1e-12, 1e-13 / alpha)
+            sym = relerr(np.array([a2]), np.array([a1]))
+            assert sym < max(1e-12, 1e-13 / alpha)
 
 
 def test_full_size_2d_solve():
@@ -293,22 +301,23 @@ def test_maxit_reports_not_converged():
 
 
 def test_alpha_one_abc_mode():
-    """alpha = 1 (ABC preconditioner |C_1|): either rejected as singular or equal to the
-    oracle's fast path, which at alpha = 1 is |C_1|^{-1} (pinned densely on the CPU)."""
+    """alpha = 1 (ABC preconditioner |C_1|) equals the oracle's fast path, which at
+    alpha = 1 is |C_1|^{-1} (pinned densely on the CPU).  At (1D, 63, 64) the smallest
+    |Sigma| is about 3e-4 of the largest, far above the 1e-12 singularity threshold, so
+    the handle must be created."""
     d, N, nt = 1, 63, 64
     tau = 1.0 / nt
     st, h = aao.aao_create(d, N, nt, tau, 1.0, raw_status=True)
-    if st == aao.AAO_ESINGULAR:
-        return
-    assert st == aao.AAO_OK
+    assert st == aao.AAO_OK, aao.aao_last_error()
     try:
         x = W.random_field((nt, N), seed=700)
         ref = OF.ABACPreconditioner(d, N, nt, tau, 1.0).apply(x)
         xt = cu(x)
-        zt = torch.empty_like(xt)
+        zt = guards.guarded_empty(xt.shape)
         aao.aao_apply_prec(h, xt, zt)
         torch.cuda.synchronize()
-        assert relerr(zt.cpu().numpy(), ref) < 1e-10
+        assert relerr(zt.cpu().numpy(), ref) < gates.fp64("prec", d, N, nt, 1.0)
+        guards.check(zt)
     finally:
         aao.aao_destroy(h)
 

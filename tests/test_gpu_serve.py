@@ -63,6 +63,11 @@ def test_mixed_requests_equal_solo_solves():
         aao.aao_serve_destroy(srv)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["peak_pool_bytes"] <= stats["budget"]
+    # the iterations ran as grouped launches: more than one request per round on average,
+    # and a round's launch count bounded by the step kernels plus one time launch per
+    # (precision, n) bucket, whatever the number of requests in it
+    assert stats["round_problems"] > stats["rounds"], stats
+    assert stats["grouped_launches"] <= stats["rounds"] * (7 + 10), stats
     for (r, p, f, p0, p1, x), res in zip(reqs, results):
         st, info, xs = _solo(p, r["tol"])
         assert st == aao.AAO_OK
@@ -163,3 +168,44 @@ def test_served_precisions_equal_solo_solves():
         assert res["iters"] == info[0]["iters"]
         assert np.array_equal(x.cpu().numpy(), xs.cpu().numpy()), prec
         assert res["relres_true"] <= r["tol"]
+
+
+def test_requests_arriving_during_a_solve_are_admitted_and_finish_first():
+    """Continuous admission: small requests submitted while a large solve is on the GPU
+    start before it finishes and complete before it (their size class has its own
+    stream and rounds), and every result equals its solo solve."""
+    big = W.config_2d(N=255, nt=512, alpha=1e-6)
+    small = [W.served_problem(dict(d=1, N=N, nt=nt, c2=c2, tol=1e-8, seed=3000 + i), alpha=1e-6)
+             for i, (N, nt, c2) in enumerate([(63, 64, 1.0), (127, 128, 2.2), (255, 64, 0.5), (63, 256, 1.7)])]
+    srv = aao.aao_serve_create(16 << 30, 8)
+    try:
+        # warm the pool (handles, kernels) so the timing below is the solves'
+        for p in [big] + small:
+            assert _submit_wait(srv, p)[0] == aao.AAO_OK
+        bufs = []
+        xb = torch.empty((big.nt, big.m), dtype=torch.float64, device="cuda")
+        fb, b0, b1 = cu(big.f), cu(big.psi0), cu(big.psi1)
+        tb = aao.aao_serve_submit(srv, 2, big.N, big.nt, big.tau, 1e-6, 1.0, 1e-8, 100, fb, b0, b1, xb)
+        time.sleep(2e-3)
+        ts = []
+        for p in small:
+            f, p0, p1 = cu(p.f), cu(p.psi0), cu(p.psi1)
+            x = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
+            bufs.append((p, f, p0, p1, x))
+            ts.append(aao.aao_serve_submit(srv, 1, p.N, p.nt, p.tau, 1e-6, p.c2, 1e-8, 100, f, p0, p1, x))
+        st, rb = aao.aao_serve_wait(srv, tb, 120.0)
+        assert st == aao.AAO_OK
+        rs = []
+        for t in ts:
+            st, r = aao.aao_serve_wait(srv, t, 120.0)
+            assert st == aao.AAO_OK
+            rs.append(r)
+    finally:
+        aao.aao_serve_destroy(srv)
+    for r in rs:
+        assert r["t_start"] < rb["t_done"], (r, rb)
+        assert r["t_done"] < rb["t_done"], (r, rb)
+    for (p, f, p0, p1, x), r in zip(bufs, rs):
+        st, info, xs = _solo(p, 1e-8)
+        assert st == aao.AAO_OK and info["iters"] == r["iters"]
+        assert np.array_equal(x.cpu().numpy(), xs)

@@ -7,6 +7,7 @@ import os
 import numpy as np
 import pytest
 
+import gates
 import workloads as W
 from oracle import fast as OF
 
@@ -14,8 +15,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2306_03574_gb300 as aao  # noqa: E402
-
-EPS32 = 2.0 ** -24
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -54,7 +53,8 @@ def _time_ref(d, N, nt, x):
 def test_time_variants(d, N, nt, monkeypatch):
     x = W.random_field((nt, N ** d), seed=1700 + nt + N)
     ref = _time_ref(d, N, nt, x)
-    tol32 = 64 * EPS32 * np.log2(nt) * ALPHA ** (-(nt - 1) / nt)
+    tol32 = gates.fp32("time", d, N, nt, ALPHA)
+    tol64 = gates.fp64("time", d, N, nt, ALPHA)
     outs = []
     for v in range(8):
         monkeypatch.setenv("AAO_TIME_VARIANT", f"{v},{v}")
@@ -66,7 +66,7 @@ def test_time_variants(d, N, nt, monkeypatch):
                 torch.cuda.synchronize()
                 y = yt.cpu().numpy()
             if prec == aao.AAO_PREC_FP64:
-                assert relerr(y, ref) < 1e-12, (v, "fp64")
+                assert relerr(y, ref) < tol64, (v, "fp64")
                 outs.append(y)
             else:
                 assert relerr(y, ref) < tol32, (v, "fp32")
@@ -84,7 +84,7 @@ def test_dst_and_prec_variants(d, N, nt, monkeypatch):
     S = OF.dst_matrix(N)
     ref_dst = OF.apply_space(x, S, d, N)
     ref_prec = OF.ABACPreconditioner(d, N, nt, 1.0 / nt, ALPHA).apply(x)
-    tol32 = 64 * EPS32 * np.log2(nt) * ALPHA ** (-(nt - 1) / nt)
+    tol32 = gates.fp32("prec", d, N, nt, ALPHA)
     for dv in range(2):
         for tv in (1, 5):
             monkeypatch.setenv("AAO_DST_VARIANT", str(dv))
