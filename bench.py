@@ -142,6 +142,25 @@ def algorithmic_bytes(cls: str, d: int, N: int, nt: int, unknowns: int, vec_byte
     return 0.0
 
 
+_ALU_PEAKS = {}
+
+
+def alu_peaks_measured():
+    """FP64 (DFMA) and FP32 (FFMA) rates of the library's FMA-loop probe on this GPU,
+    measured once per process (outside any timed region)."""
+    if not _ALU_PEAKS:
+        try:
+            import paper_2306_03574_gb300 as aao
+            f64, ms64 = aao.aao_alu_peak(aao.AAO_PREC_FP64, 1 << 14)
+            f32, ms32 = aao.aao_alu_peak(aao.AAO_PREC_FP32_IR, 1 << 18)
+            _ALU_PEAKS.update(fp64_tflops=f64, fp32_tflops=f32, fp64_ms=ms64, fp32_ms=ms32,
+                              how="aao_alu_peak: 8 blocks x 256 threads per SM, 8 independent FMA chains "
+                                  "per thread, best of 3 CUDA-event timings")
+        except Exception as e:  # statistics only
+            _ALU_PEAKS["error"] = repr(e)[:200]
+    return dict(_ALU_PEAKS)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -517,7 +536,7 @@ def cufft_comparison(s, p, dev, reps=10):
 
 
 
-def run_gpu(args, world, rank, local):
+def run_gpu(args, world, rank, local, emit=True):
     import numpy as np
     import torch
 
@@ -646,6 +665,14 @@ def run_gpu(args, world, rank, local):
                 "peak_note": "measured copy bandwidth (of measured)"}
 
     roofline = roof(dom)
+    if roofline["bound"] == "alu":
+        # the unit-count peak stays the denominator; the measured FMA-loop rate is reported beside it
+        meas = alu_peaks_measured()
+        if meas:
+            roofline["peak_measured_fma_loop"] = meas
+            key = "fp64_tflops" if roofline["peak"] == FP64_PEAK_TFLOPS else "fp32_tflops"
+            if meas.get(key):
+                roofline["frac_of_measured_fma_loop"] = roofline["achieved"] / meas[key]
     var = None
     if variants:
         var = variants["time_variant"] if dom.startswith("time") else (
@@ -737,12 +764,13 @@ def run_gpu(args, world, rank, local):
             "gpu_launches": launches, "clocks": clk, "kernels": kern, "kernel_variants": variants,
         }
         out.update(extra)
-        print(json.dumps(out), flush=True)
+        if emit:
+            print(json.dumps(out), flush=True)
     s.close()
-    return 0
+    return out
 
 
-def run_served(args, world, rank, local):
+def run_served(args, world, rank, local, emit=True):
     """Served stream: Poisson arrivals (mean --rate/s, default 200, seeded) of 1D/2D requests with mixed
     sizes, wave speeds and tolerances, admitted under a 120 GB HBM budget; replayed in
     real time; latency = completion - submission on the server's clock."""
@@ -850,9 +878,117 @@ def run_served(args, world, rank, local):
         "unknowns_per_s": unknowns / (t_last - t_first), "iters_mean": float(np.mean([res["iters"] for _, res in ok])),
         "server": stats, "sample_equal_alone": same, "sample_size": len(sample),
     }
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
+
+
+def run_profile_case(args):
+    """A small fixed case for ncu captures and variant timing: --reps applications of
+    one step (--what) of one problem size through the C ABI, on seeded N(0,1) data.
+    With --sweep, every time-kernel variant of the precision is timed with CUDA events
+    (best of --reps after a warm-up) and one JSON line is printed."""
+    import numpy as np
+    import torch
+
+    import paper_2306_03574_gb300 as aao
+
+    if args.time_variant is not None:
+        os.environ["AAO_TIME_VARIANT"] = f"{args.time_variant},{args.time_variant},{args.time_variant}"
+    if args.dst_variant is not None:
+        os.environ["AAO_DST_VARIANT"] = str(args.dst_variant)
+    prec = {"fp64": aao.AAO_PREC_FP64, "fp32": aao.AAO_PREC_FP32_IR, "f32x2": aao.AAO_PREC_F32X2}[args.precision]
+    d, N, nt = args.d, args.N, args.nt
+    m = N ** d
+    rng = np.random.default_rng(1)
+    x = torch.from_numpy(rng.standard_normal((args.nrhs, nt, m))).cuda()
+    y = torch.empty_like(x)
+
+    def one(s):
+        if args.what == "prec":
+            s.apply_prec(x, y)
+        elif args.what == "time":
+            s.apply_time(x, y)
+        elif args.what == "dst":
+            s.apply_dst(x, y)
+        elif args.what == "op":
+            s.apply_op(x, y)
+        else:
+            s.apply_op(x, y)
+            st, info = s.solve(y, x, rtol=1e-8, maxit=50)
+            assert st == aao.AAO_OK, info
+
+    if not args.sweep:
+        with aao.Solver(d, N, nt, 1.0 / nt, args.pc_alpha, precision=prec, nrhs_max=args.nrhs) as s:
+            for _ in range(args.reps):
+                one(s)
+            torch.cuda.synchronize()
+        print("ok")
+        return 0
+    nvar = {"fp64": 8, "fp32": 18, "f32x2": 12}[args.precision]
+    times = {}
+    for v in range(nvar):
+        os.environ["AAO_TIME_VARIANT"] = f"{v & 7},{v},{v}"
+        with aao.Solver(d, N, nt, 1.0 / nt, args.pc_alpha, precision=prec, nrhs_max=args.nrhs) as s:
+            one(s)
+            torch.cuda.synchronize()
+            best = 1e30
+            for _ in range(max(args.reps, 3)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                one(s)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            times[v] = best
+    print(json.dumps({"profile_case": {"d": d, "N": N, "nt": nt, "nrhs": args.nrhs, "precision": args.precision,
+                                       "what": args.what}, "variant_ms": times,
+                      "wait_timeouts": aao.aao_wait_timeouts()}), flush=True)
     return 0
+
+
+def _summary(line):
+    """The figures of one workload's line that the default line carries."""
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "iters_per_solve", "relres_true",
+            "unknown_iters_per_s", "roofline", "clocks", "e2e", "error_vs_exact", "vs_fp64_gpu", "gpu_launches",
+            "latency_ms", "completed", "failed", "offered_rate", "sample_equal_alone", "sample_size",
+            "kernel_variants")
+    out = {k: line[k] for k in keep if k in line}
+    out["config"] = line.get("config")
+    if "server" in line:
+        srv = line["server"]
+        out["server"] = {k: srv[k] for k in ("rounds", "round_problems", "grouped_launches", "handles_created",
+                                             "evictions", "peak_pool_bytes") if k in srv}
+    return out
+
+
+def run_extra_workloads(args, world, rank, local):
+    """The other configurations of the benchmark, each measured as its own workload
+    (own warm-up, CUDA-event timing, clocks and roofline): the 1D 63 x 64 latency case,
+    the 2D 511^2 x 512 mixed-precision case and a served Poisson stream."""
+    import copy
+    res = {}
+    saved = dict(WORKLOAD), WORKLOAD_NAME[0]
+    for name, steps in (("1d63_fp64", 50), ("2d511_mixed", 10)):
+        a = copy.copy(args)
+        a.workload, a.steps, a.warmup, a.no_cpu_baseline = name, steps, 3, True
+        WORKLOAD.clear()
+        WORKLOAD.update(WORKLOADS[name])
+        WORKLOAD_NAME[0] = name
+        try:
+            res[name] = _summary(run_gpu(a, world, rank, local, emit=False))
+        except Exception as e:  # report, keep the default line
+            res[name] = {"error": repr(e)[:300]}
+    WORKLOAD.clear()
+    WORKLOAD.update(saved[0])
+    WORKLOAD_NAME[0] = saved[1]
+    a = copy.copy(args)
+    a.workload, a.requests = "served", args.served_requests
+    try:
+        res["served"] = _summary(run_served(a, world, rank, local, emit=False))
+    except Exception as e:
+        res["served"] = {"error": repr(e)[:300]}
+    return res
 
 
 def main():
@@ -864,6 +1000,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served"], default="2d255_fp64")
     ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
+    ap.add_argument("--served-requests", type=int, default=400,
+                    help="requests of the served stream reported under 'workloads' by the default run")
     ap.add_argument("--slots", type=int, default=8, help="served workload: concurrent solves")
     ap.add_argument("--rate", type=float, default=200.0, help="served workload: mean Poisson arrival rate (1/s)")
     ap.add_argument("--serve-precision", choices=["fp64", "f32x2"], default="fp64",
@@ -871,9 +1009,27 @@ def main():
     ap.add_argument("--alpha", type=float, default=None)
     ap.add_argument("--graph", type=int, default=1,
                     help="1: solve loop captured in a CUDA graph (device-side while loop); 0: host-driven")
+    ap.add_argument("--extra-workloads", type=int, default=1,
+                    help="default workload at N=1: also measure the 1D latency, 2D 511^2 x 512 mixed-precision "
+                         "and served-stream workloads and report them under 'workloads'")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: pick the time/DST kernel variants by measurement before warm-up; 0: defaults")
+    pc = ap.add_argument_group("--profile-case: one small fixed case (ncu captures, variant timing)")
+    pc.add_argument("--profile-case", action="store_true")
+    pc.add_argument("--what", choices=["prec", "time", "dst", "op", "solve"], default="prec")
+    pc.add_argument("--d", type=int, default=2)
+    pc.add_argument("--N", type=int, default=255)
+    pc.add_argument("--nt", type=int, default=256)
+    pc.add_argument("--nrhs", type=int, default=1)
+    pc.add_argument("--precision", choices=["fp64", "fp32", "f32x2"], default="fp64")
+    pc.add_argument("--pc-alpha", type=float, default=1e-6)
+    pc.add_argument("--reps", type=int, default=1)
+    pc.add_argument("--time-variant", type=int, default=None)
+    pc.add_argument("--dst-variant", type=int, default=None)
+    pc.add_argument("--sweep", action="store_true", help="time every time-kernel variant")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.workload != "served":
         WORKLOAD.clear()
         WORKLOAD.update(WORKLOADS[args.workload])
@@ -887,10 +1043,17 @@ def main():
         rc = run_reference(args, world, rank)
     elif args.workload == "served":
         world, rank, local = dist_setup(args.gpus, "nccl")
-        rc = run_served(args, world, rank, local)
+        run_served(args, world, rank, local)
+        rc = 0
     else:
         world, rank, local = dist_setup(args.gpus, "nccl")
-        rc = run_gpu(args, world, rank, local)
+        if args.workload == "2d255_fp64" and args.extra_workloads and world == 1:
+            out = run_gpu(args, world, rank, local, emit=False)
+            out["workloads"] = run_extra_workloads(args, world, rank, local)
+            print(json.dumps(out), flush=True)
+        else:
+            run_gpu(args, world, rank, local)
+        rc = 0
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -354,6 +354,20 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen);
 /* Number of kernel launches this handle has issued since creation (statistics). */
 uint64_t aao_launch_count(const aao_handle* h);
 
+/* Arithmetic-rate probe (statistics for rooflines, not part of the method): times, with
+ * CUDA events on a private stream, a kernel of independent fused multiply-add chains on
+ * every SM (8 blocks of 256 threads per SM, 8 chains per thread, `iters` steps per
+ * chain; best of 3 after a warm-up) and returns the rate in TFLOP/s (2 flops per FMA)
+ * and the kernel time.  precision: AAO_PREC_FP64 (DFMA) or AAO_PREC_FP32_IR (FFMA).
+ * Synchronous; allocates one scalar.  Errors: AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA. */
+aao_status aao_alu_peak(int precision, int iters, double* tflops, double* ms);
+
+/* Kernels that stage data with bulk asynchronous copies wait on an mbarrier with a
+ * bounded number of polls; a wait that runs out is counted here (process-wide, current
+ * device) and its tile is abandoned.  0 in a healthy run; 0xFFFFFFFF if the counter
+ * cannot be read.  Statistics, not part of the method. */
+unsigned int aao_wait_timeouts(void);
+
 /* Per-kernel timing (statistics, not part of the method).  While enabled, every
  * kernel the handle launches is bracketed by two CUDA events recorded on the
  * stream it is launched on; aao_profile_read synchronises on those events and

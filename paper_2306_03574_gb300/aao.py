@@ -19,7 +19,7 @@ __all__ = [
     "aao_create", "aao_destroy", "aao_set_coefficient", "aao_autotune", "aao_workspace_bytes", "aao_build_rhs", "aao_apply_op",
     "aao_apply_prec", "aao_apply_dst", "aao_apply_time", "aao_minres_solve", "aao_solve_host",
     "aao_residual_norm", "aao_residual_norm_noalloc",
-    "aao_launch_count", "aao_status_str", "aao_last_error", "aao_profile_enable", "aao_profile_read",
+    "aao_launch_count", "aao_wait_timeouts", "aao_alu_peak", "aao_status_str", "aao_last_error", "aao_profile_enable", "aao_profile_read",
     "Solver", "aao_serve_create", "aao_serve_submit", "aao_serve_poll", "aao_serve_wait",
     "aao_serve_stats", "aao_serve_destroy",
 ]
@@ -112,6 +112,8 @@ def lib() -> ctypes.CDLL:
             "aao_minres_solve": ([p, p, p, i, i, d, i, ctypes.POINTER(aao_solve_info), p], i),
             "aao_solve_host": ([p, p, p, p, p, i, d, i, ctypes.POINTER(aao_solve_info), p], i),
             "aao_launch_count": ([p], ctypes.c_uint64),
+            "aao_wait_timeouts": ([], ctypes.c_uint),
+            "aao_alu_peak": ([i, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i),
             "aao_residual_norm": ([p, p, p, p, i, p], i),
             "aao_residual_norm_noalloc": ([ctypes.POINTER(aao_grid), i, d, p, p, p, i, p], i),
             "aao_noalloc_last_error": ([], ctypes.c_char_p),
@@ -249,6 +251,16 @@ def aao_workspace_bytes(h) -> int:
 def aao_launch_count(h) -> int:
     return int(lib().aao_launch_count(h))
 
+
+def aao_wait_timeouts() -> int:
+    return int(lib().aao_wait_timeouts())
+
+
+def aao_alu_peak(precision: int, iters: int = 1 << 16):
+    """(TFLOP/s, ms) of the FMA-loop probe in FP64 (AAO_PREC_FP64) or FP32 (AAO_PREC_FP32_IR)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().aao_alu_peak(precision, iters, ctypes.byref(tf), ctypes.byref(ms)), "aao_alu_peak")
+    return tf.value, ms.value
 
 
 def aao_build_rhs(h, f, psi0, psi1, b, nrhs: int = 1, stream=None) -> None:

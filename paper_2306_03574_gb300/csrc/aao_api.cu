@@ -1116,7 +1116,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     int c = -1;
     if (sscanf(tv, "%d,%d,%d", &a, &b, &c) >= 1) {
       P.time_variant64 = a & 7;
-      P.time_variant32 = (b >= 0 ? b : a) & 7;
+      P.time_variant32 = (b >= 0 ? b : a) & 31;
       P.time_variant_ff = (c >= 0 ? c : (b >= 0 ? b : a)) & 15;
     }
   }
@@ -1261,7 +1261,7 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
       bool found = false;
       while (fscanf(fh, "%d %d %d %d %d %d", &d, &N, &n, &pr, &tv, &dv) == 6)
         if (d == P.d && N == P.N && n == P.n && pr == prec) {
-          tvar(P, prec) = tv & (prec == AAO_PREC_F32X2 ? 15 : 7);
+          tvar(P, prec) = tv & (prec == AAO_PREC_FP64 ? 7 : 31);
           P.dst_variant = dv & 1;
           found = true;
         }
@@ -1300,8 +1300,10 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // The default variants stay unless another is faster by more than 1 % (run-to-run
   // timing noise is a few tenths of a percent; near-ties keep the choice reproducible).
   const int def_tv = tvar(P, prec), def_dv = P.dst_variant;
-  // double-float has four more time variants (8..11: interleaved layout, no staged table)
-  const int ntv = prec == AAO_PREC_F32X2 ? 12 : 8;
+  // double-float has four more time variants (8..11: interleaved layout, no staged table),
+  // the FP32 pipeline on FP64 vectors ten (8..15: the tile staged by bulk copies; 16, 17:
+  // variants 5 and 7 with integer conversions)
+  const int ntv = prec == AAO_PREC_F32X2 ? 12 : prec == AAO_PREC_FP32_IR ? 18 : 8;
   std::vector<float> tt(ntv), td(2);
   for (int v = 0; v < ntv; ++v) {
     tvar(P, prec) = v;

@@ -29,6 +29,7 @@
 #include <type_traits>
 
 #include "aao_internal.cuh"
+#include "convert_bits.cuh"
 #include "dfloat.cuh"
 #include "fft_smem.cuh"
 
@@ -131,9 +132,12 @@ template <int L> struct FoldScaling<double, L> { static constexpr bool value = t
 template <int L> struct FoldScaling<float, L> { static constexpr bool value = L <= 256; };
 
 // Tile `tile` (mode pairs tile*NS ..) of one right-hand side: in and out point at it.
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG>
+// ICVT: FP64 <-> FP32 conversions of the load and store by integer operations
+// (convert_bits.cuh) instead of cvt instructions on the FP64 pipe.
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG, bool ICVT = false>
 __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArgs& a, const PrecTables<R>& tb,
                                           int tile) {
+  using CV = Cvt<R, TIO, ICVT>;
   using C = typename Cplx<R>::T;
   using Y = SLay<L, NS, LAY>;
   constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
@@ -164,8 +168,8 @@ __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArg
     const TIO* p = in + (long long)t * m + sa;
     const R di = FOLD ? R(1) : dinv[t];
     C z;
-    z.x = (sa < m) ? (FOLD ? R(p[0]) : R(p[0]) * di) : R();
-    z.y = (sa + 1 < m) ? (FOLD ? R(p[1]) : R(p[1]) * di) : R();
+    z.x = (sa < m) ? (FOLD ? CV::load(p[0]) : CV::load(p[0]) * di) : R();
+    z.y = (sa + 1 < m) ? (FOLD ? CV::load(p[1]) : CV::load(p[1]) * di) : R();
     cbuf[Y::at(q, t)] = z;
   }
   if constexpr (STAGED) cp_async_wait_all();
@@ -199,19 +203,19 @@ __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArg
     TIO* p = out + (long long)t * m + sa;
     const C z = cbuf[Y::at(q, t)];
     const R di = dinv[t];
-    if (sa < m) p[0] = TIO(z.x * di);
-    if (sa + 1 < m) p[1] = TIO(z.y * di);
+    if (sa < m) p[0] = CV::store(z.x * di);
+    if (sa + 1 < m) p[1] = CV::store(z.y * di);
   }
 }
 
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1>
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   const long long rb = (long long)blockIdx.y * L * a.m;
-  time_body<R, TIO, L, NS, NT, FFTV, LAY, STG>(in + rb, out + rb, a, tb, blockIdx.x);
+  time_body<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT>(in + rb, out + rb, a, tb, blockIdx.x);
 }
 
 // Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1>
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false>
 static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
   constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
@@ -221,7 +225,7 @@ static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int n
   a.m = P.m;
   a.n = P.n;
   a.npairs = P.npairs;
-  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY, STG>;
+  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
   kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
@@ -233,6 +237,11 @@ static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrh
   const int v = std::is_same<R, double>::value  ? P.time_variant64
                 : std::is_same<R, float>::value ? P.time_variant32
                                                 : P.time_variant_ff;
+  if constexpr (std::is_same<R, float>::value && std::is_same<TIO, double>::value) {
+    // FP32 arithmetic on FP64 vectors: 16, 17 = variants 5, 7 with integer conversions
+    if (v == 16) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, true>(P, in, out, nrhs, s);
+    if (v == 17) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, true>(P, in, out, nrhs, s);
+  }
   if constexpr (std::is_same<R, dfl>::value) {
     if (v & 8) {  // interleaved layout without the staged table slice
       switch (v & 3) {

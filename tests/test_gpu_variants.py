@@ -56,9 +56,9 @@ def test_time_variants(d, N, nt, monkeypatch):
     tol32 = gates.fp32("time", d, N, nt, ALPHA)
     tol64 = gates.fp64("time", d, N, nt, ALPHA)
     outs = []
-    for v in range(8):
-        monkeypatch.setenv("AAO_TIME_VARIANT", f"{v},{v}")
-        for prec in (aao.AAO_PREC_FP64, aao.AAO_PREC_FP32_IR):
+    for v in range(18):  # FP32 on FP64 vectors: 8..15 bulk-staged tile, 16, 17 integer conversions
+        monkeypatch.setenv("AAO_TIME_VARIANT", f"{v & 7},{v}")
+        for prec in (aao.AAO_PREC_FP64, aao.AAO_PREC_FP32_IR) if v < 8 else (aao.AAO_PREC_FP32_IR,):
             with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=prec) as s:
                 xt = cu(x)
                 yt = torch.empty_like(xt)
@@ -73,6 +73,41 @@ def test_time_variants(d, N, nt, monkeypatch):
     # the FP64 variants differ only in rounding order
     for y in outs[1:]:
         assert np.abs(y - outs[0]).max() <= 1e-13 * np.abs(outs[0]).max()
+    assert aao.aao_wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("d,N,nt", [(2, 63, 64), (1, 255, 256), (1, 511, 512), (2, 127, 128)])
+def test_bulk_staged_time_kernel_guards_and_alignment(d, N, nt, monkeypatch):
+    """The bulk-staged FP32 kernels (variants 8..15) write nothing outside their output
+    (guard bands at both ends), and a vector that is only 8-byte aligned -- which bulk
+    copies cannot address -- is served by the register-staged variant with the same
+    gate; every variant's result passes the FP32 gate."""
+    import guards
+    m = N ** d
+    x = W.random_field((nt, m), seed=1750 + nt + N)
+    ref = _time_ref(d, N, nt, x)
+    tol32 = gates.fp32("time", d, N, nt, ALPHA)
+    for v in range(8, 16):
+        monkeypatch.setenv("AAO_TIME_VARIANT", f"3,{v}")
+        with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=aao.AAO_PREC_FP32_IR) as s:
+            xt = guards.guarded_copy(x)
+            yt = guards.guarded_empty(xt.shape)
+            s.apply_time(xt, yt)
+            torch.cuda.synchronize()
+            assert relerr(yt.cpu().numpy(), ref) < tol32, v
+            guards.check(yt)
+            guards.check(xt)
+            # 8-byte aligned views: one double into a larger buffer
+            big = torch.zeros(x.size + 2, dtype=torch.float64, device="cuda")
+            xv = big[1:1 + x.size].view(nt, m)
+            xv.copy_(torch.from_numpy(x))
+            outb = torch.zeros(x.size + 2, dtype=torch.float64, device="cuda")
+            yv = outb[1:1 + x.size].view(nt, m)
+            s.apply_time(xv, yv)
+            torch.cuda.synchronize()
+            assert relerr(yv.cpu().numpy(), ref) < tol32, (v, "8-byte aligned")
+            assert outb[0].item() == 0.0 and outb[-1].item() == 0.0
+    assert aao.aao_wait_timeouts() == 0
 
 
 @pytest.mark.parametrize("d,N,nt", [(2, 63, 64), (2, 127, 64), (2, 255, 64), (2, 511, 64), (3, 63, 64)])
