@@ -1300,10 +1300,11 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // The default variants stay unless another is faster by more than 1 % (run-to-run
   // timing noise is a few tenths of a percent; near-ties keep the choice reproducible).
   const int def_tv = tvar(P, prec), def_dv = P.dst_variant;
-  // double-float has four more time variants (8..11: interleaved layout, no staged table),
-  // the FP32 pipeline on FP64 vectors ten (8..15: the tile staged by bulk copies; 16, 17:
-  // variants 5 and 7 with integer conversions)
-  const int ntv = prec == AAO_PREC_F32X2 ? 12 : prec == AAO_PREC_FP32_IR ? 18 : 8;
+  // double-float has six more time variants (8..11: interleaved layout, no staged table;
+  // 12, 13: 9 and 11 with batched loads), the FP32 pipeline on FP64 vectors fourteen
+  // (8..15: the tile staged by bulk copies; 16, 17: variants 5 and 7 with integer
+  // conversions; 18..21: with batched loads)
+  const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 22 : 8;
   std::vector<float> tt(ntv), td(2);
   for (int v = 0; v < ntv; ++v) {
     tvar(P, prec) = v;

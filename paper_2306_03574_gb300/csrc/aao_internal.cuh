@@ -61,12 +61,14 @@ struct Plan {
   int d = 0, N = 0, M = 0, n = 0, m = 0, npairs = 0;
   double tau = 0, alpha = 0, c2 = 0, h = 0;
   double coef = 0;  // c2 tau^2 / (2 h^2): L w = w - coef * (sum of neighbour differences)
-  // time-kernel variant per precision: bit 0 = radix-16 stage plan, bit 1 = half-size
-  // tile, bit 2 = interleaved padded shared-memory layout with the table slice staged
-  // in shared memory.  Defaults measured on GB300: FP64 (FP64-pipe bound) radix-16 +
-  // half tile; FP32 radix-16 + full tile + interleaved layout (bank conflicts and
-  // table-load latency dominate otherwise).
-  int time_variant64 = 3, time_variant32 = 5, time_variant_ff = 9;
+  // time-kernel variant per precision (k_time.cuh): for 0..7, bit 0 = radix-16 stage
+  // plan, bit 1 = half-size tile, bit 2 = interleaved padded shared-memory layout with
+  // the table slice staged in shared memory; higher numbers add batched loads, bulk-copy
+  // staging or integer conversions (k_time.cuh, k_time32.cu).  Defaults measured on
+  // GB300: FP64 (FP64-pipe bound) radix-16 + half tile; FP32 on FP64 vectors variant 5
+  // (radix-16, full tile, interleaved) with batched loads; double-float radix-16, full
+  // tile, interleaved without the staged table, with batched loads.
+  int time_variant64 = 3, time_variant32 = 18, time_variant_ff = 12;
   // DST stage plan: 0 = radix-4, 1 = radix-16 first
   int dst_variant = 1;
   PrecTables<double> t64;
@@ -253,8 +255,9 @@ int group_yt_tiles(int m);
 int group_yt_blocks(int n, int m);
 int group_wx_blocks(int m);
 int group_vu_blocks(int n, int m);
-// time-kernel tiles of a problem with m modes for time length L and variant v
-int time_tiles(int L, int variant, int m);
+// time-kernel tiles of a problem with m modes in the grouped launch of precision R
+template <typename R>
+int group_time_tiles(int L, int m);
 
 // The grouped launches of one MINRES iteration (d_round: device copy of the round's
 // descriptors; totals: the launch's block counts from the host copy).

@@ -7,7 +7,9 @@
 // pool; requests behind one that must wait are not held up by it.  Handles come from a
 // pool bounded by an HBM budget.  A provisioner thread creates missing handles and
 // destroys evicted ones (least recently used idle handles first), so cudaMalloc, cudaFree
-// and the synchronous table build of aao_create never run on the worker's path.  A
+// and the synchronous table build of aao_create never run on the worker's path; when a
+// request takes the last idle handle of its shape, a spare is provisioned in the
+// background while the pool stays within half the budget.  A
 // pooled handle is re-bound to the request's tau, alpha and c2 on the device without a
 // host synchronisation (its |Sigma| check is read when the request completes).
 //
@@ -307,24 +309,21 @@ struct aao_server {
           std::lock_guard<std::mutex> lk2(mu);
           st.evictions++;
         }
-        PoolEntry* e = new PoolEntry();
-        e->dim = q.dim;
-        e->N = q.N;
-        e->nt = q.nt;
-        e->precision = q.precision;
-        e->bytes = need;
-        pool.push_back(e);
-        pool_bytes += need;
-        to_create.push_back(e);
-        {
-          std::lock_guard<std::mutex> lk2(mu);
-          st.handles_created++;
-        }
-        publish_pool_stats();
-        prov_cv.notify_all();
+        post_create(q, need);
         return false;  // admitted once the handle is ready
       }
       pe->busy = true;
+      // Spare: when this takes the last idle handle of its shape, provision another in
+      // the background if the pool stays within half the budget (spares never evict) and
+      // more than one request can be in flight, so that the next request of the shape
+      // does not wait for a handle to be created.
+      bool other = false;
+      for (PoolEntry* e : pool)
+        if (e != pe && e->dim == q.dim && e->N == q.N && e->nt == q.nt && e->precision == q.precision &&
+            !e->busy && e->fail == AAO_OK)
+          other = true;
+      const size_t need = aaoi_estimate_bytes(q.dim, q.N, q.nt, q.precision) + (size_t)unknowns_of(q) * sizeof(double);
+      if (!other && max_slots > 1 && pool_bytes + need <= budget / 2) post_create(q, need);
     }
     SizeClass& C = cls[c];
     aao_status s = aaoi_rebind_async(pe->h, q.tau, q.alpha, q.c2, C.stream);
@@ -346,6 +345,25 @@ struct aao_server {
     st.admitted++;
     st.in_flight = in_flight;
     return true;
+  }
+
+  // queue the creation of a handle of q's shape (pool_mu held); its bytes are reserved now
+  void post_create(const aao_request& q, size_t need) {
+    PoolEntry* e = new PoolEntry();
+    e->dim = q.dim;
+    e->N = q.N;
+    e->nt = q.nt;
+    e->precision = q.precision;
+    e->bytes = need;
+    pool.push_back(e);
+    pool_bytes += need;
+    to_create.push_back(e);
+    {
+      std::lock_guard<std::mutex> lk2(mu);
+      st.handles_created++;
+    }
+    publish_pool_stats();
+    prov_cv.notify_all();
   }
 
   void release(PoolEntry* pe) {
@@ -436,12 +454,12 @@ struct aao_server {
       if (aaoi_precision(h) == AAO_PREC_F32X2 && v == aao::group_time_variant<aao::dfl>()) {
         aao::TimeGroup<aao::dfl>& T = H.tff[bk];
         aaoi_time_entry_ff(h, par, &T.e[ntff[bk]]);
-        T.tile[ntff[bk] + 1] = T.tile[ntff[bk]] + aao::time_tiles(L, v, P.m);
+        T.tile[ntff[bk] + 1] = T.tile[ntff[bk]] + aao::group_time_tiles<aao::dfl>(L, P.m);
         ++ntff[bk];
       } else if (aaoi_precision(h) == AAO_PREC_FP64 && v == aao::group_time_variant<double>()) {
         aao::TimeGroup<double>& T = H.t64[bk];
         aaoi_time_entry64(h, par, &T.e[nt64[bk]]);
-        T.tile[nt64[bk] + 1] = T.tile[nt64[bk]] + aao::time_tiles(L, v, P.m);
+        T.tile[nt64[bk] + 1] = T.tile[nt64[bk]] + aao::group_time_tiles<double>(L, P.m);
         ++nt64[bk];
       } else {
         solo_time.emplace_back(h, par);

@@ -245,34 +245,60 @@ struct VarArgs {
   const double* face;  // d * (N+1) * N^(d-1)
 };
 
+// The coefficients on the faces left/right of point s along each axis (constant in time,
+// so a thread loads them once for its whole run of time levels).
+struct Faces {
+  double xl, xr, yl, yr, zl, zr;
+};
+
 template <int D>
-__device__ __forceinline__ double apply_La(const double* __restrict__ v, int s, int ix, int iy, int iz,
-                                           const VarArgs& a) {
+__device__ __forceinline__ Faces load_faces(int ix, int iy, int iz, const VarArgs& a) {
   const int N = a.N;
   const long long fsz = (long long)(N + 1) * (D == 1 ? 1 : (D == 2 ? N : N * N));
-  const double c = v[s];
-  double acc;
+  Faces f{};
   {  // x faces: index (iz*N + iy)*(N+1) + f
-    const double* F = a.face;
     const long long base = ((long long)iz * N + iy) * (N + 1);
-    const double aL = F[base + ix], aR = F[base + ix + 1];
-    const double wl = ix > 0 ? v[s - 1] : 0.0, wr = ix < N - 1 ? v[s + 1] : 0.0;
-    acc = fma(aR, c - wr, aL * (c - wl));
+    f.xl = a.face[base + ix];
+    f.xr = a.face[base + ix + 1];
   }
   if (D >= 2) {  // y faces: index (iz*(N+1) + f)*N + ix
     const double* F = a.face + fsz;
     const long long base = (long long)iz * (N + 1);
-    const double aL = F[(base + iy) * N + ix], aR = F[(base + iy + 1) * N + ix];
-    const double wl = iy > 0 ? v[s - N] : 0.0, wr = iy < N - 1 ? v[s + N] : 0.0;
-    acc = fma(aR, c - wr, fma(aL, c - wl, acc));
+    f.yl = F[(base + iy) * N + ix];
+    f.yr = F[(base + iy + 1) * N + ix];
   }
   if (D >= 3) {  // z faces: index (f*N + iy)*N + ix
     const double* F = a.face + 2 * fsz;
-    const double aL = F[((long long)iz * N + iy) * N + ix], aR = F[((long long)(iz + 1) * N + iy) * N + ix];
-    const double wl = iz > 0 ? v[s - N * N] : 0.0, wr = iz < N - 1 ? v[s + N * N] : 0.0;
-    acc = fma(aR, c - wr, fma(aL, c - wl, acc));
+    f.zl = F[((long long)iz * N + iy) * N + ix];
+    f.zr = F[((long long)(iz + 1) * N + iy) * N + ix];
   }
-  return fma(a.cv, acc, c);
+  return f;
+}
+
+template <int D>
+__device__ __forceinline__ double apply_La_f(const double* __restrict__ v, int s, int ix, int iy, int iz, int N,
+                                             double cv, const Faces& f) {
+  const double c = v[s];
+  double acc;
+  {
+    const double wl = ix > 0 ? v[s - 1] : 0.0, wr = ix < N - 1 ? v[s + 1] : 0.0;
+    acc = fma(f.xr, c - wr, f.xl * (c - wl));
+  }
+  if (D >= 2) {
+    const double wl = iy > 0 ? v[s - N] : 0.0, wr = iy < N - 1 ? v[s + N] : 0.0;
+    acc = fma(f.yr, c - wr, fma(f.yl, c - wl, acc));
+  }
+  if (D >= 3) {
+    const double wl = iz > 0 ? v[s - N * N] : 0.0, wr = iz < N - 1 ? v[s + N * N] : 0.0;
+    acc = fma(f.zr, c - wr, fma(f.zl, c - wl, acc));
+  }
+  return fma(cv, acc, c);
+}
+
+template <int D>
+__device__ __forceinline__ double apply_La(const double* __restrict__ v, int s, int ix, int iy, int iz,
+                                           const VarArgs& a) {
+  return apply_La_f<D>(v, s, ix, iy, iz, a.N, a.cv, load_faces<D>(ix, iy, iz, a));
 }
 
 template <int D, int MODE>
@@ -290,10 +316,11 @@ __global__ void __launch_bounds__(YT_NT) k_yt_var(const double* __restrict__ x, 
     const int iy = (D >= 2) ? (s / N) % N : 0;
     const int iz = (D >= 3) ? s / (N * N) : 0;
     const double* xr = x + rb;
+    const Faces fc = load_faces<D>(ix, iy, iz, a);
     double Lv1 = 0.0, Lv2 = 0.0, v1 = 0.0;
     for (int i = max(0, i0 - 2); i < i1; ++i) {
       const double* vi = xr + (long long)i * m;
-      const double Lv = apply_La<D>(vi, s, ix, iy, iz, a);
+      const double Lv = apply_La_f<D>(vi, s, ix, iy, iz, N, a.cv, fc);
       if (i >= i0) {
         const double o = fma(-2.0, v1, Lv + Lv2);
         const long long idx = rb + (long long)(n - 1 - i) * m + s;

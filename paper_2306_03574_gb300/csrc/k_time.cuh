@@ -134,7 +134,10 @@ template <int L> struct FoldScaling<float, L> { static constexpr bool value = L 
 // Tile `tile` (mode pairs tile*NS ..) of one right-hand side: in and out point at it.
 // ICVT: FP64 <-> FP32 conversions of the load and store by integer operations
 // (convert_bits.cuh) instead of cvt instructions on the FP64 pipe.
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG, bool ICVT = false>
+// PRELOAD > 0: the tile's loads batched in registers, PRELOAD tasks (two values each)
+// per batch, every load of a batch issued before the first is converted.
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG, bool ICVT = false,
+          int PRELOAD = 0>
 __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArgs& a, const PrecTables<R>& tb,
                                           int tile) {
   using CV = Cvt<R, TIO, ICVT>;
@@ -154,23 +157,68 @@ __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArg
   const int s0 = tile * (2 * NS);
   const int p0 = tile * NS;
   if constexpr (STAGED) stage_table<L, NS, NT>(tab, tb.ab, a.npairs, p0);
-  for (int i = tid; i < L; i += NT) {
-    tw[i] = tb.tw_time[i];
-    dinv[i] = tb.dinv[i];
-    d2[i] = tb.d2[i];
-  }
-  __syncthreads();
+  if constexpr (PRELOAD > 0) {
+    // Batches of PB tasks: every load of a batch is issued (into registers) before the
+    // first is converted, the first batch before the table loads and the barrier.
+    constexpr int TPT = NS * L / NT;
+    constexpr int PB = TPT < PRELOAD ? TPT : PRELOAD;
+    static_assert(NS * L % NT == 0 && TPT % PB == 0, "load batches");
+    TIO xa[PB], xb[PB];
+    auto load = [&](int b0) {
+#pragma unroll
+      for (int i = 0; i < PB; ++i) {
+        const int task = tid + (b0 + i) * NT;
+        const int q = task % NS, t = task / NS;
+        const int sa = s0 + 2 * q;
+        const TIO* p = in + (long long)t * m + sa;
+        xa[i] = sa < m ? p[0] : TIO(0);
+        xb[i] = sa + 1 < m ? p[1] : TIO(0);
+      }
+    };
+    auto put = [&](int b0) {
+#pragma unroll
+      for (int i = 0; i < PB; ++i) {
+        const int task = tid + (b0 + i) * NT;
+        const int q = task % NS, t = task / NS;
+        const R di = FOLD ? R(1) : dinv[t];
+        C z;
+        z.x = FOLD ? CV::load(xa[i]) : CV::load(xa[i]) * di;
+        z.y = FOLD ? CV::load(xb[i]) : CV::load(xb[i]) * di;
+        cbuf[Y::at(q, t)] = z;
+      }
+    };
+    load(0);
+    for (int i = tid; i < L; i += NT) {
+      tw[i] = tb.tw_time[i];
+      dinv[i] = tb.dinv[i];
+      d2[i] = tb.d2[i];
+    }
+    __syncthreads();
+    put(0);
+#pragma unroll 1
+    for (int b0 = PB; b0 < TPT; b0 += PB) {
+      load(b0);
+      put(b0);
+    }
+  } else {
+    for (int i = tid; i < L; i += NT) {
+      tw[i] = tb.tw_time[i];
+      dinv[i] = tb.dinv[i];
+      d2[i] = tb.d2[i];
+    }
+    __syncthreads();
 
-  // load, scaled by D^{-1} here or (FOLD) by the first FFT stage
-  for (int task = tid; task < NS * L; task += NT) {
-    const int q = task % NS, t = task / NS;
-    const int sa = s0 + 2 * q;
-    const TIO* p = in + (long long)t * m + sa;
-    const R di = FOLD ? R(1) : dinv[t];
-    C z;
-    z.x = (sa < m) ? (FOLD ? CV::load(p[0]) : CV::load(p[0]) * di) : R();
-    z.y = (sa + 1 < m) ? (FOLD ? CV::load(p[1]) : CV::load(p[1]) * di) : R();
-    cbuf[Y::at(q, t)] = z;
+    // load, scaled by D^{-1} here or (FOLD) by the first FFT stage
+    for (int task = tid; task < NS * L; task += NT) {
+      const int q = task % NS, t = task / NS;
+      const int sa = s0 + 2 * q;
+      const TIO* p = in + (long long)t * m + sa;
+      const R di = FOLD ? R(1) : dinv[t];
+      C z;
+      z.x = (sa < m) ? (FOLD ? CV::load(p[0]) : CV::load(p[0]) * di) : R();
+      z.y = (sa + 1 < m) ? (FOLD ? CV::load(p[1]) : CV::load(p[1]) * di) : R();
+      cbuf[Y::at(q, t)] = z;
+    }
   }
   if constexpr (STAGED) cp_async_wait_all();
   __syncthreads();
@@ -208,14 +256,16 @@ __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArg
   }
 }
 
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false>
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false,
+          int PRELOAD = 0>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   const long long rb = (long long)blockIdx.y * L * a.m;
-  time_body<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT>(in + rb, out + rb, a, tb, blockIdx.x);
+  time_body<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD>(in + rb, out + rb, a, tb, blockIdx.x);
 }
 
 // Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false>
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false,
+          int PRELOAD = 0>
 static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
   constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
@@ -225,7 +275,7 @@ static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int n
   a.m = P.m;
   a.n = P.n;
   a.npairs = P.npairs;
-  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT>;
+  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
   kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
@@ -237,12 +287,26 @@ static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrh
   const int v = std::is_same<R, double>::value  ? P.time_variant64
                 : std::is_same<R, float>::value ? P.time_variant32
                                                 : P.time_variant_ff;
+  if constexpr (std::is_same<R, float>::value && std::is_same<TIO, float>::value) {
+    // FP32 vectors: the variants of the FP64-vector kernel above 7 map to the classic
+    // layout of their tile (full: 5, half: 7)
+    if (v >= 8) return (v & 1) ? time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1>(P, in, out, nrhs, s)
+                               : time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1>(P, in, out, nrhs, s);
+  }
   if constexpr (std::is_same<R, float>::value && std::is_same<TIO, double>::value) {
-    // FP32 arithmetic on FP64 vectors: 16, 17 = variants 5, 7 with integer conversions
+    // FP32 arithmetic on FP64 vectors: 16, 17 = variants 5, 7 with integer conversions;
+    // 18, 19 = variants 5, 7 with the loads batched 8 tasks at a time, 20, 21 16 at a time
     if (v == 16) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, true>(P, in, out, nrhs, s);
     if (v == 17) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, true>(P, in, out, nrhs, s);
+    if (v == 18) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, false, 8>(P, in, out, nrhs, s);
+    if (v == 19) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, false, 8>(P, in, out, nrhs, s);
+    if (v == 20) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, false, 16>(P, in, out, nrhs, s);
+    if (v == 21) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, false, 16>(P, in, out, nrhs, s);
   }
   if constexpr (std::is_same<R, dfl>::value) {
+    // 12, 13 = variants 9, 11 with the loads batched 8 tasks at a time
+    if (v == 12) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, 0, false, 8>(P, in, out, nrhs, s);
+    if (v == 13) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, 0, false, 8>(P, in, out, nrhs, s);
     if (v & 8) {  // interleaved layout without the staged table slice
       switch (v & 3) {
         case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0, 1, 0>(P, in, out, nrhs, s);

@@ -10,7 +10,7 @@ namespace aao {
 
 namespace {
 
-template <typename R, int L, int NS, int NT, int FFTV, int LAY, int STG>
+template <typename R, int L, int NS, int NT, int FFTV, int LAY, int STG, int PRE>
 __global__ void __launch_bounds__(NT) k_g_time(const TimeGroup<R>* __restrict__ g) {
   const int r = group_find(g->tile, g->count, blockIdx.x);
   const TimeGroupEntry<R>& e = g->e[r];
@@ -19,41 +19,49 @@ __global__ void __launch_bounds__(NT) k_g_time(const TimeGroup<R>* __restrict__ 
   a.m = e.m;
   a.n = L;
   a.npairs = e.npairs;
-  time_body<R, double, L, NS, NT, FFTV, LAY, STG>(e.in, e.out, a, e.tb, blockIdx.x - g->tile[r]);
+  time_body<R, double, L, NS, NT, FFTV, LAY, STG, false, PRE>(e.in, e.out, a, e.tb, blockIdx.x - g->tile[r]);
 }
 
-template <typename R, int L, int NS, int NT, int FFTV, int LAY, int STG = -1>
-cudaError_t g_time_cfg(const TimeGroup<R>* d, int total, cudaStream_t s) {
-  using C = typename Cplx<R>::T;
-  constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
-  const size_t smem = sizeof(C) * (SLay<L, NS, LAY>::size + (STAGED ? 2 * NS * (L / 2 + 1) : 0) + L) +
-                      2 * sizeof(R) * L;
-  auto kern = k_g_time<R, L, NS, NT, FFTV, LAY, STG>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<total, NT, smem, s>>>(d);
-  return cudaGetLastError();
-}
+// The variant of each precision that has a grouped form -- the precision's default --
+// and its configuration, which must equal the solo launch's (k_time.cuh,
+// time_launch_L): FP64 variant 3 (radix-16 stage plan, 2048/L mode pairs x 128 threads,
+// sequence-major layout); double-float variant 12 (radix-16, 4096/L x 256, interleaved
+// layout without the staged table slice, loads batched 8 tasks at a time).  A problem
+// whose handle runs another variant takes its solo launch instead.
+template <typename R> struct GroupTimeCfg;
+template <> struct GroupTimeCfg<double> {
+  static constexpr int V = 3, PAIRS = 2048, NT = 128, FFTV = 1, LAY = 0, STG = -1, PRE = 0;
+};
+template <> struct GroupTimeCfg<dfl> {
+  static constexpr int V = 12, PAIRS = 4096, NT = 256, FFTV = 1, LAY = 1, STG = 0, PRE = 8;
+};
 
-// Only the default variant of each precision has a grouped form, with the tile shape of
-// its solo launch (FP64, variant 3: radix-16 stage plan, 2048/L mode pairs x 128 threads,
-// sequence-major layout; double-float, variant 9: radix-16, 4096/L x 256, interleaved
-// layout without the staged table slice); a problem whose handle runs another variant
-// takes its solo launch instead (group_time_variant).
 template <typename R, int L>
 cudaError_t g_time_L(const TimeGroup<R>* d, int total, cudaStream_t s) {
-  if constexpr (std::is_same<R, dfl>::value) return g_time_cfg<R, L, 4096 / L, 256, 1, 1, 0>(d, total, s);
-  else return g_time_cfg<R, L, 2048 / L, 128, 1, 0>(d, total, s);
+  using G = GroupTimeCfg<R>;
+  using C = typename Cplx<R>::T;
+  constexpr int NS = G::PAIRS / L;
+  constexpr bool STAGED = G::STG < 0 ? G::LAY == 1 : G::STG == 1;
+  const size_t smem = sizeof(C) * (SLay<L, NS, G::LAY>::size + (STAGED ? 2 * NS * (L / 2 + 1) : 0) + L) +
+                      2 * sizeof(R) * L;
+  auto kern = k_g_time<R, L, NS, G::NT, G::FFTV, G::LAY, G::STG, G::PRE>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<total, G::NT, smem, s>>>(d);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-int time_tiles(int L, int variant, int m) {
-  const int ns = (variant & 2) ? 2048 / L : 4096 / L;
+template <typename R>
+int group_time_tiles(int L, int m) {
+  const int ns = GroupTimeCfg<R>::PAIRS / L;
   return (m + 2 * ns - 1) / (2 * ns);
 }
+template int group_time_tiles<double>(int, int);
+template int group_time_tiles<dfl>(int, int);
 
 template <typename R>
-int group_time_variant() { return std::is_same<R, dfl>::value ? 9 : 3; }
+int group_time_variant() { return GroupTimeCfg<R>::V; }
 template int group_time_variant<double>();
 template int group_time_variant<dfl>();
 

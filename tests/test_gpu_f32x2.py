@@ -67,7 +67,7 @@ def test_f32x2_time_variants(d, N, nt, monkeypatch):
     m = N ** d
     x = W.random_field((nt, m), seed=2400 + nt)
     ref = OF.time_part_modes(d, N, nt, tau, alpha, x, np.arange(m))
-    for v in range(12):  # 8..11: interleaved layout without the staged table slice
+    for v in range(14):  # 8..11: interleaved layout without the staged table slice; 12, 13 batched loads
         monkeypatch.setenv("AAO_TIME_VARIANT", f"{v},{v},{v}")
         with aao.Solver(d, N, nt, tau, alpha, precision=aao.AAO_PREC_F32X2) as s:
             xt = cu(x)

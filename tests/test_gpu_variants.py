@@ -56,7 +56,9 @@ def test_time_variants(d, N, nt, monkeypatch):
     tol32 = gates.fp32("time", d, N, nt, ALPHA)
     tol64 = gates.fp64("time", d, N, nt, ALPHA)
     outs = []
-    for v in range(18):  # FP32 on FP64 vectors: 8..15 bulk-staged tile, 16, 17 integer conversions
+    # FP32 on FP64 vectors: 8..15 bulk-staged tile, 16, 17 integer conversions, 18..21
+    # loads batched ahead of their conversion
+    for v in range(22):
         monkeypatch.setenv("AAO_TIME_VARIANT", f"{v & 7},{v}")
         for prec in (aao.AAO_PREC_FP64, aao.AAO_PREC_FP32_IR) if v < 8 else (aao.AAO_PREC_FP32_IR,):
             with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=prec) as s:
@@ -78,7 +80,8 @@ def test_time_variants(d, N, nt, monkeypatch):
 
 @pytest.mark.parametrize("d,N,nt", [(2, 63, 64), (1, 255, 256), (1, 511, 512), (2, 127, 128)])
 def test_bulk_staged_time_kernel_guards_and_alignment(d, N, nt, monkeypatch):
-    """The bulk-staged FP32 kernels (variants 8..15) write nothing outside their output
+    """The bulk-staged FP32 kernels (variants 8..15) and the batched-load ones (18..21)
+    write nothing outside their output
     (guard bands at both ends), and a vector that is only 8-byte aligned -- which bulk
     copies cannot address -- is served by the register-staged variant with the same
     gate; every variant's result passes the FP32 gate."""
@@ -87,7 +90,7 @@ def test_bulk_staged_time_kernel_guards_and_alignment(d, N, nt, monkeypatch):
     x = W.random_field((nt, m), seed=1750 + nt + N)
     ref = _time_ref(d, N, nt, x)
     tol32 = gates.fp32("time", d, N, nt, ALPHA)
-    for v in range(8, 16):
+    for v in list(range(8, 16)) + [18, 19, 20, 21]:
         monkeypatch.setenv("AAO_TIME_VARIANT", f"3,{v}")
         with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=aao.AAO_PREC_FP32_IR) as s:
             xt = guards.guarded_copy(x)
