@@ -126,7 +126,8 @@ typedef struct aao_handle aao_handle;
  * Tuning overrides (environment, read here; for measurements and tests):
  *   AAO_TIME_VARIANT="v64[,v32[,vff]]" sets the time-kernel variant per precision
  *   (the numbering of aao_autotune; a missing entry repeats the previous one), and
- *   AAO_DST_VARIANT="0|1" the DST stage plan.  Every variant computes the same values.
+ *   AAO_DST_VARIANT="0..3" the DST variant (bit 0: radix-16-first stage plan, bit 1:
+ *   batched loads).  Every variant computes the same values.
  * Errors: AAO_EINVAL, AAO_EUNSUPPORTED, AAO_ENOMEM, AAO_ECUDA, AAO_ESINGULAR. */
 aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha,
                       aao_scheme scheme, const aao_opts* opts, aao_handle** out);
@@ -338,9 +339,12 @@ const char* aao_serve_last_error(void);
 /* Autotuner: pick, for this handle's shape and precision, the fastest variant of the
  * time-pipeline kernel (FFT stage plan: radix-4 or radix-16 first; tile: 4096/n or
  * 2048/n mode pairs per CTA; shared-memory layout: sequence-major or interleaved and
- * padded, the latter with or without a staged slice of the spectral table in
- * double-float mode) and of the DST kernel (radix-4 or radix-16 stage plan) by
- * timing each on the handle's workspace with CUDA events (the work of the kernels is
+ * padded, the latter with or without a staged slice of the spectral table; and, for
+ * the FP32 and double-float pipelines on FP64 vectors, loads batched ahead of their
+ * conversion, bulk-copy staging of the tile or integer conversions, and, in FP32, the
+ * spectral table read from memory or computed on the fly) and of the DST
+ * kernel (radix-4 or radix-16 stage plan, with or without batched loads) by timing
+ * each on the handle's workspace with CUDA events (the work of the kernels is
  * the same in every variant; only speed differs).  The default variant is kept unless
  * another is more than 1 % faster, so near-ties give the same choice on every run.
  * tune_file (host string, may be

@@ -63,6 +63,7 @@ struct aao_handle {
   double* dinv64 = nullptr; double* d264 = nullptr; double2* ab64 = nullptr;
   float2* tw_space32 = nullptr; float* sinw32 = nullptr; float2* tw_time32 = nullptr;
   float* dinv32 = nullptr; float* d232 = nullptr; float2* ab32 = nullptr;
+  float2* wq32 = nullptr; float* lm132 = nullptr;  // per-frequency Sigma terms, Lambda - 1 (FP32)
   dfl2* tw_time_ff = nullptr; dfl* dinv_ff = nullptr; dfl* d2_ff = nullptr; dfl2* ab_ff = nullptr;
   dfl2* tw_space_ff = nullptr; dfl* sinw_ff = nullptr;
   // workspace (nrhs_max * n * m doubles each)
@@ -743,7 +744,7 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
 // terms of Sigma (wq, 2n), D_alpha^{-1} and D_alpha^2 (n each) and Lambda (m), computed in
 // long double and rounded; also sets the plan's tau, alpha, c2 and stencil coefficient.
 void param_tables(Plan& P, double tau, double alpha, double c2, double2* wq, double* dinv, double* d2,
-                  double* lam) {
+                  double* lam, float* lm1_32 = nullptr) {
   const int nt = P.n, M = P.M;
   P.tau = tau;
   P.alpha = alpha;
@@ -780,6 +781,7 @@ void param_tables(Plan& P, double tau, double alpha, double c2, double2* wq, dou
     long double sum = 0.0L;
     for (int ax = 0; ax < P.d; ++ax) { sum += mul[rest % P.N]; rest /= P.N; }
     lam[(size_t)s_] = (double)(1.0L + ct * sum);
+    if (lm1_32) lm1_32[(size_t)s_] = (float)(ct * sum);  // Lambda_s - 1 without cancellation
   }
 }
 
@@ -787,7 +789,8 @@ void param_tables(Plan& P, double tau, double alpha, double c2, double2* wq, dou
 // asynchronous copy): uploads, the spectral table (and its double-float split), and the
 // per-block min/max |Sigma| copied to mm_host (nblocks pairs).
 aao_status bind_tables(aao_handle* h, const double2* wq, const double* dinv, const double* d2,
-                       const double* lam, const float* dinv32, const float* d232, const dfl* dinv_ff,
+                       const double* lam, const float* dinv32, const float* d232, const float2* wq32,
+                       const float* lm132, const dfl* dinv_ff,
                        const dfl* d2_ff, double* mm_host, int* nblocks, cudaStream_t s) {
   Plan& P = h->P;
   const size_t nt = (size_t)P.n;
@@ -799,6 +802,8 @@ aao_status bind_tables(aao_handle* h, const double2* wq, const double* dinv, con
   if (fp32) {
     AAO_CK(cudaMemcpyAsync(h->dinv32, dinv32, nt * sizeof(float), cudaMemcpyHostToDevice, s));
     AAO_CK(cudaMemcpyAsync(h->d232, d232, nt * sizeof(float), cudaMemcpyHostToDevice, s));
+    AAO_CK(cudaMemcpyAsync(h->wq32, wq32, 2 * nt * sizeof(float2), cudaMemcpyHostToDevice, s));
+    AAO_CK(cudaMemcpyAsync(h->lm132, lm132, (size_t)P.m * sizeof(float), cudaMemcpyHostToDevice, s));
   }
   if (h->precision == AAO_PREC_F32X2) {
     AAO_CK(cudaMemcpyAsync(h->dinv_ff, dinv_ff, nt * sizeof(dfl), cudaMemcpyHostToDevice, s));
@@ -833,12 +838,15 @@ aao_status set_params(aao_handle* h, double tau, double alpha, double c2, cudaSt
   const int nt = P.n;
   std::vector<double2> wq(2 * (size_t)nt);
   std::vector<double> dinv(nt), d2(nt), lam((size_t)P.m);
-  param_tables(P, tau, alpha, c2, wq.data(), dinv.data(), d2.data(), lam.data());
+  std::vector<float> lm132((size_t)P.m);
+  param_tables(P, tau, alpha, c2, wq.data(), dinv.data(), d2.data(), lam.data(), lm132.data());
   const std::vector<float> dinv32 = to_f(dinv), d232 = to_f(d2);
+  const std::vector<float2> wq32 = to_f2(wq);
   const std::vector<dfl> dinv_ff = to_df(dinv), d2_ff = to_df(d2);
   std::vector<double> mm((size_t)2 * h->mm_blocks);
   int nb = 0;
-  AAO_TRY(bind_tables(h, wq.data(), dinv.data(), d2.data(), lam.data(), dinv32.data(), d232.data(),
+  AAO_TRY(bind_tables(h, wq.data(), dinv.data(), d2.data(), lam.data(), dinv32.data(), d232.data(), wq32.data(),
+                      lm132.data(),
                       dinv_ff.data(), d2_ff.data(), mm.data(), &nb, s));
   AAO_CK(cudaStreamSynchronize(s));  // pageable host arrays: wait before they go
   return check_sigma(mm.data(), nb);
@@ -937,8 +945,8 @@ aao_status aaoi_rebind_async(aao_handle* h, double tau, double alpha, double c2,
       h->pin_dinv_ff[t] = dfl(h->pin_dinv[t]);
       h->pin_d2_ff[t] = dfl(h->pin_d2[t]);
     }
-  return bind_tables(h, h->pin_wq, h->pin_dinv, h->pin_d2, h->pin_lam, nullptr, nullptr, h->pin_dinv_ff,
-                     h->pin_d2_ff, h->pin_mm, &h->pin_nb, s);
+  return bind_tables(h, h->pin_wq, h->pin_dinv, h->pin_d2, h->pin_lam, nullptr, nullptr, nullptr, nullptr,
+                     h->pin_dinv_ff, h->pin_d2_ff, h->pin_mm, &h->pin_nb, s);
 }
 
 // b = Y f, b^ = (I (x) U) b and the MINRES initialisation from a zero guess (no graph),
@@ -1111,6 +1119,9 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   P.c2 = grid->c2;
   P.h = 1.0 / (double)M;
   P.coef = P.c2 * tau * tau / (2.0 * P.h * P.h);
+  // DST default: the FP64 DST is bound by the FP64 pipe; the double-float and FP32 DSTs
+  // (the handle's DSTs in the other modes) gain from batched loads (measured on GB300)
+  P.dst_variant = o.precision == AAO_PREC_FP64 ? 1 : 3;
   if (const char* tv = getenv("AAO_TIME_VARIANT")) {  // tuning override: "v64,v32,vff"
     int a = 0, b = -1;
     int c = -1;
@@ -1120,7 +1131,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
       P.time_variant_ff = (c >= 0 ? c : (b >= 0 ? b : a)) & 15;
     }
   }
-  if (const char* dv = getenv("AAO_DST_VARIANT")) P.dst_variant = atoi(dv) & 1;
+  if (const char* dv = getenv("AAO_DST_VARIANT")) P.dst_variant = atoi(dv) & 3;
 
   auto bail = [&](aao_status st) { delete h; return st; };
 
@@ -1163,7 +1174,8 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   if (fp32) {
     if ((st = h->alloc(&h->tw_space32, M)) || (st = h->alloc(&h->sinw32, M / 2 + 1)) ||
         (st = h->alloc(&h->tw_time32, nt)) || (st = h->alloc(&h->dinv32, nt)) ||
-        (st = h->alloc(&h->d232, nt)) || (st = h->alloc(&h->ab32, tabn)))
+        (st = h->alloc(&h->d232, nt)) || (st = h->alloc(&h->ab32, tabn)) ||
+        (st = h->alloc(&h->wq32, 2 * (size_t)nt)) || (st = h->alloc(&h->lm132, (size_t)P.m)))
       return bail(st);
   }
   const size_t vl = (size_t)h->nrhs_max * (size_t)nt * P.m;
@@ -1223,6 +1235,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
     if (fp32) {
       P.t32.tw_space = h->tw_space32; P.t32.sinw = h->sinw32; P.t32.tw_time = h->tw_time32;
       P.t32.dinv = h->dinv32; P.t32.d2 = h->d232; P.t32.ab = h->ab32;
+      P.t32.wq = h->wq32; P.t32.lm1 = h->lm132; P.t32.inv2n = (float)(1.0 / (2.0 * nt));
       P.t32.cq = (float)(cM / 4.0L);
     }
     if (ff_dst) {
@@ -1262,7 +1275,7 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
       while (fscanf(fh, "%d %d %d %d %d %d", &d, &N, &n, &pr, &tv, &dv) == 6)
         if (d == P.d && N == P.N && n == P.n && pr == prec) {
           tvar(P, prec) = tv & (prec == AAO_PREC_FP64 ? 7 : 31);
-          P.dst_variant = dv & 1;
+          P.dst_variant = dv & 3;
           found = true;
         }
       fclose(fh);
@@ -1301,11 +1314,12 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // timing noise is a few tenths of a percent; near-ties keep the choice reproducible).
   const int def_tv = tvar(P, prec), def_dv = P.dst_variant;
   // double-float has six more time variants (8..11: interleaved layout, no staged table;
-  // 12, 13: 9 and 11 with batched loads), the FP32 pipeline on FP64 vectors fourteen
+  // 12, 13: 9 and 11 with batched loads), the FP32 pipeline on FP64 vectors sixteen
   // (8..15: the tile staged by bulk copies; 16, 17: variants 5 and 7 with integer
-  // conversions; 18..21: with batched loads)
-  const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 22 : 8;
-  std::vector<float> tt(ntv), td(2);
+  // conversions; 18..21: with batched loads; 22, 23: 18, 19 with the spectral table
+  // computed on the fly instead of read)
+  const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 24 : 8;
+  std::vector<float> tt(ntv), td(4);
   for (int v = 0; v < ntv; ++v) {
     tvar(P, prec) = v;
     tt[v] = timeit([&]() {
@@ -1319,14 +1333,16 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
     if (tt[v] < tt[best_tv]) best_tv = v;
   if (!(tt[best_tv] < 0.99f * tt[def_tv])) best_tv = def_tv;
   tvar(P, prec) = best_tv;
-  for (int v = 0; v < 2; ++v) {
+  for (int v = 0; v < 4; ++v) {
     P.dst_variant = v;
     td[v] = timeit([&]() {
       if (prec == AAO_PREC_F32X2 || prec == AAO_PREC_FP32_IR) launch_dst_axis_ff(P, h->vv, h->vz, 0, 1, s, nullptr);
       else launch_dst_axis<double>(P, h->vv, h->vz, 0, 1, s, nullptr);
     });
   }
-  int best_dv = td[1] < td[0] ? 1 : 0;
+  int best_dv = 0;
+  for (int v = 1; v < 4; ++v)
+    if (td[v] < td[best_dv]) best_dv = v;
   if (!(td[best_dv] < 0.99f * td[def_dv])) best_dv = def_dv;
   P.dst_variant = best_dv;
   if (chosen) {

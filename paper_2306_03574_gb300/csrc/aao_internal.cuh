@@ -55,6 +55,10 @@ struct PrecTables {
   const R* d2 = nullptr;        // n entries, alpha^{2t/n}
   const C* ab = nullptr;        // (n/2+1) * npairs * 2 entries: A_k, B_k per mode pair
   R cq = 0;                     // sqrt(2/M) / 4
+  // inputs of the spectral factors computed on the fly (FP32 tables only):
+  const C* wq = nullptr;        // 2n entries: (1 - a theta^k)^2, 1 + a^2 theta^{2k}
+  const R* lm1 = nullptr;       // m entries: Lambda_s - 1
+  R inv2n = 0;                  // 1/(2n)
 };
 
 struct Plan {
@@ -69,7 +73,8 @@ struct Plan {
   // (radix-16, full tile, interleaved) with batched loads; double-float radix-16, full
   // tile, interleaved without the staged table, with batched loads.
   int time_variant64 = 3, time_variant32 = 18, time_variant_ff = 12;
-  // DST stage plan: 0 = radix-4, 1 = radix-16 first
+  // DST variant: bit 0 = radix-16-first stage plan (else radix-4), bit 1 = batched
+  // pre-processing loads (aao_create: 1 for FP64 handles, 3 otherwise)
   int dst_variant = 1;
   PrecTables<double> t64;
   PrecTables<float> t32;

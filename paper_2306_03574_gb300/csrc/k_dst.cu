@@ -36,7 +36,9 @@ struct DstArgs {
   long long nouter; // strided axis: number of outer blocks
 };
 
-template <typename R, typename TIO, int M, int NS, int NT, bool STRIDED, int FFTV>
+// PRE: the pre-processing loads of a thread issued in batches of 4 tasks (16 values)
+// before any of them is used, the first batch ahead of the table loads and the barrier.
+template <typename R, typename TIO, int M, int NS, int NT, bool STRIDED, int FFTV, bool PRE = false>
 __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
   constexpr int H = M / 2;
@@ -50,8 +52,6 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
 
   const int tid = threadIdx.x;
   const int N = a.N;
-  for (int i = tid; i < M; i += NT) tw[i] = tb.tw_space[i];
-  for (int i = tid; i <= H; i += NT) sw[i] = tb.sinw[i];
 
   // line addressing
   long long line0 = 0, obase = 0;
@@ -62,39 +62,46 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
     obase = (long long)blockIdx.x * ((long long)a.st * N);
     i0 = blockIdx.y * (2 * NS);
   }
-  __syncthreads();
 
   // ---- pre-processing: y'_j, y'_{M-j} for j = 1..M/2 of lines a, b ----
-  const R cq = tb.cq;
-  for (int task = tid; task < NS * H; task += NT) {
-    int q, j;
+  // task -> (line pair q, index j); the four inputs x_j, x_{M-j} of lines a, b
+  auto task_qj = [&](int task, int& q, int& j) {
     if (!STRIDED) { q = task / H; j = task % H + 1; }
     else { q = task % NS; j = task / NS + 1; }
-    R xa0 = R(), xa1 = R(), xb0 = R(), xb1 = R();  // x_j, x_{M-j} of lines a, b
+  };
+  auto load4 = [&](int task, TIO& a0, TIO& a1, TIO& b0, TIO& b1) {
+    int q, j;
+    task_qj(task, q, j);
+    a0 = a1 = b0 = b1 = TIO(0);
     if (!STRIDED) {
       const long long la = line0 + 2 * q;
       if (la < a.nlines) {
         const TIO* p = in + la * N;
-        xa0 = R(p[j - 1]);
-        xa1 = R(p[M - j - 1]);
+        a0 = p[j - 1];
+        a1 = p[M - j - 1];
       }
       if (la + 1 < a.nlines) {
         const TIO* p = in + (la + 1) * N;
-        xb0 = R(p[j - 1]);
-        xb1 = R(p[M - j - 1]);
+        b0 = p[j - 1];
+        b1 = p[M - j - 1];
       }
     } else {
       const int ia = i0 + 2 * q;
       const TIO* p = in + obase + ia;
       if (ia < a.st) {
-        xa0 = R(p[(long long)(j - 1) * a.st]);
-        xa1 = R(p[(long long)(M - j - 1) * a.st]);
+        a0 = p[(long long)(j - 1) * a.st];
+        a1 = p[(long long)(M - j - 1) * a.st];
       }
       if (ia + 1 < a.st) {
-        xb0 = R(p[(long long)(j - 1) * a.st + 1]);
-        xb1 = R(p[(long long)(M - j - 1) * a.st + 1]);
+        b0 = p[(long long)(j - 1) * a.st + 1];
+        b1 = p[(long long)(M - j - 1) * a.st + 1];
       }
     }
+  };
+  auto weigh = [&](int task, R xa0, R xa1, R xb0, R xb1) {
+    int q, j;
+    task_qj(task, q, j);
+    const R cq = tb.cq;
     const R w = sw[j];
     const R sa = xa0 + xa1, ta = cq * (xa0 - xa1);
     const R sb = xb0 + xb1, tbb = cq * (xb0 - xb1);
@@ -103,6 +110,34 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
     hi.x = fmadd(w, sa, -ta); hi.y = fmadd(w, sb, -tbb);
     cbuf[q * M + j] = lo;
     if (j != H) cbuf[q * M + M - j] = hi;
+  };
+  if constexpr (PRE) {
+    constexpr int TPT = NS * H / NT, PB = 4;
+    static_assert(NS * H % NT == 0 && TPT % PB == 0, "pre-processing batches");
+    TIO x[PB][4];
+#pragma unroll
+    for (int i = 0; i < PB; ++i) load4(tid + i * NT, x[i][0], x[i][1], x[i][2], x[i][3]);
+    for (int i = tid; i < M; i += NT) tw[i] = tb.tw_space[i];
+    for (int i = tid; i <= H; i += NT) sw[i] = tb.sinw[i];
+    __syncthreads();
+#pragma unroll 1
+    for (int b0 = 0; b0 < TPT; b0 += PB) {
+      if (b0 > 0) {
+#pragma unroll
+        for (int i = 0; i < PB; ++i) load4(tid + (b0 + i) * NT, x[i][0], x[i][1], x[i][2], x[i][3]);
+      }
+#pragma unroll
+      for (int i = 0; i < PB; ++i) weigh(tid + (b0 + i) * NT, R(x[i][0]), R(x[i][1]), R(x[i][2]), R(x[i][3]));
+    }
+  } else {
+    for (int i = tid; i < M; i += NT) tw[i] = tb.tw_space[i];
+    for (int i = tid; i <= H; i += NT) sw[i] = tb.sinw[i];
+    __syncthreads();
+    for (int task = tid; task < NS * H; task += NT) {
+      TIO a0, a1, b0, b1;
+      load4(task, a0, a1, b0, b1);
+      weigh(task, R(a0), R(a1), R(b0), R(b1));
+    }
   }
   for (int q = tid; q < NS; q += NT) { C z; z.x = R(); z.y = R(); cbuf[q * M] = z; }
   __syncthreads();
@@ -181,7 +216,7 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
   }
 }
 
-template <typename R, typename TIO, int M, int FFTV>
+template <typename R, typename TIO, int M, int FFTV, bool PRE>
 static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs,
                                  cudaStream_t s) {
   using C = typename Cplx<R>::T;
@@ -198,7 +233,7 @@ static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axi
     a.nlines = total / P.N;
     a.st = 1;
     a.nouter = 0;
-    auto kern = k_dst<R, TIO, M, NS, NT, false, FFTV>;
+    auto kern = k_dst<R, TIO, M, NS, NT, false, FFTV, PRE>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const long long nb = (a.nlines + 2 * NS - 1) / (2 * NS);
     kern<<<dim3((unsigned)nb), NT, smem, s>>>(in, out, a, tb);
@@ -206,7 +241,7 @@ static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axi
     a.st = (int)stride;
     a.nouter = total / (stride * P.N);
     a.nlines = 0;
-    auto kern = k_dst<R, TIO, M, NS, NT, true, FFTV>;
+    auto kern = k_dst<R, TIO, M, NS, NT, true, FFTV, PRE>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int ntile = (int)((stride + 2 * NS - 1) / (2 * NS));
     kern<<<dim3((unsigned)a.nouter, (unsigned)ntile), NT, smem, s>>>(in, out, a, tb);
@@ -217,8 +252,13 @@ static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axi
 template <typename R, typename TIO, int M>
 static cudaError_t dst_launch_M(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs,
                                 cudaStream_t s) {
-  return P.dst_variant ? dst_launch_MV<R, TIO, M, 1>(P, in, out, axis, nrhs, s)
-                       : dst_launch_MV<R, TIO, M, 0>(P, in, out, axis, nrhs, s);
+  // bit 0: radix-16 stage plan; bit 1: batched pre-processing loads
+  switch (P.dst_variant & 3) {
+    case 0: return dst_launch_MV<R, TIO, M, 0, false>(P, in, out, axis, nrhs, s);
+    case 1: return dst_launch_MV<R, TIO, M, 1, false>(P, in, out, axis, nrhs, s);
+    case 2: return dst_launch_MV<R, TIO, M, 0, true>(P, in, out, axis, nrhs, s);
+    default: return dst_launch_MV<R, TIO, M, 1, true>(P, in, out, axis, nrhs, s);
+  }
 }
 
 template <typename R, typename TIO>

@@ -75,6 +75,52 @@ __device__ __forceinline__ void stage_table(C* tab, const C* __restrict__ ab, in
   cp_async_commit();
 }
 
+// Principal square root in FP32, cancellation-free: for Re z >= 0,
+// sqrt z = t + i Im(z)/(2t) with t = sqrt((|z| + Re z)/2); otherwise
+// sqrt z = |Im z|/(2t) + i sign(Im z) t with t = sqrt((|z| - Re z)/2).
+__device__ __forceinline__ float2 csqrt_principal_f(float2 z) {
+  const float r = sqrtf(fmaf(z.x, z.x, z.y * z.y));
+  float2 s;
+  if (z.x >= 0.f) {
+    const float t = sqrtf(0.5f * (r + z.x));
+    s.x = t;
+    s.y = (t > 0.f) ? z.y / (2.f * t) : 0.f;
+  } else {
+    const float t = sqrtf(0.5f * (r - z.x));
+    s.x = fabsf(z.y) / (2.f * t);
+    s.y = copysignf(t, z.y);
+  }
+  return s;
+}
+
+// The CTA's slice of the spectral table computed on the fly in FP32 instead of read
+// from memory (same layout as stage_table): for mode pair p = p0 + q and frequency k,
+// Sigma_{k,s} = (1 - a theta^k)^2 + (Lambda_s - 1)(1 + a^2 theta^{2k}) for the modes
+// s = 2p, 2p+1 (the per-frequency terms and Lambda_s - 1 come from small FP32 tables),
+// G = Sigma^{-1/2} on the principal branch, A = (G_a + G_b)/(2n), B = (G_a - G_b)/(2n)
+// (eqs. (calphaprediagform), (calphasqrtdiagform)).
+template <int L, int NS, int NT>
+__device__ __forceinline__ void compute_table(float2* tab, const PrecTables<float>& tb, int m, int p0) {
+  constexpr int H = L / 2;
+  for (int task = threadIdx.x; task < NS * (H + 1); task += NT) {
+    const int q = task % NS, k = task / NS;
+    const float2 w2 = tb.wq[2 * k], qk = tb.wq[2 * k + 1];
+    float2 G[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int sidx = 2 * (p0 + q) + e;
+      if (sidx >= m) { G[e] = make_float2(0.f, 0.f); continue; }
+      const float lm1 = tb.lm1[sidx];
+      const float2 sg = make_float2(fmaf(lm1, qk.x, w2.x), fmaf(lm1, qk.y, w2.y));
+      const float2 sq = csqrt_principal_f(sg);
+      const float qq = fmaf(sq.x, sq.x, sq.y * sq.y);
+      G[e] = make_float2(sq.x / qq, -sq.y / qq);  // 1 / sqrt(Sigma)
+    }
+    tab[2 * task] = make_float2((G[0].x + G[1].x) * tb.inv2n, (G[0].y + G[1].y) * tb.inv2n);
+    tab[2 * task + 1] = make_float2((G[0].x - G[1].x) * tb.inv2n, (G[0].y - G[1].y) * tb.inv2n);
+  }
+}
+
 // Spectral multiply of every sequence of the tile; the (A, B) entries come from the
 // staged slice tab when STAGED, else from the table in global memory.
 template <bool CONJ, int L, int NS, int NT, int LAY, bool STAGED, typename C>
@@ -136,8 +182,10 @@ template <int L> struct FoldScaling<float, L> { static constexpr bool value = L 
 // (convert_bits.cuh) instead of cvt instructions on the FP64 pipe.
 // PRELOAD > 0: the tile's loads batched in registers, PRELOAD tasks (two values each)
 // per batch, every load of a batch issued before the first is converted.
+// OTF (FP32 with PRELOAD and the staged layout): the table slice computed on the fly
+// (compute_table) while the first batch of loads is in flight, instead of read.
 template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG, bool ICVT = false,
-          int PRELOAD = 0>
+          int PRELOAD = 0, bool OTF = false>
 __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArgs& a, const PrecTables<R>& tb,
                                           int tile) {
   using CV = Cvt<R, TIO, ICVT>;
@@ -156,7 +204,8 @@ __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArg
   const int m = a.m;
   const int s0 = tile * (2 * NS);
   const int p0 = tile * NS;
-  if constexpr (STAGED) stage_table<L, NS, NT>(tab, tb.ab, a.npairs, p0);
+  static_assert(!OTF || (PRELOAD > 0 && STAGED && std::is_same<R, float>::value), "on-the-fly table");
+  if constexpr (STAGED && !OTF) stage_table<L, NS, NT>(tab, tb.ab, a.npairs, p0);
   if constexpr (PRELOAD > 0) {
     // Batches of PB tasks: every load of a batch is issued (into registers) before the
     // first is converted, the first batch before the table loads and the barrier.
@@ -188,6 +237,7 @@ __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArg
       }
     };
     load(0);
+    if constexpr (OTF) compute_table<L, NS, NT>(tab, tb, m, p0);
     for (int i = tid; i < L; i += NT) {
       tw[i] = tb.tw_time[i];
       dinv[i] = tb.dinv[i];
@@ -257,15 +307,15 @@ __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArg
 }
 
 template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false,
-          int PRELOAD = 0>
+          int PRELOAD = 0, bool OTF = false>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   const long long rb = (long long)blockIdx.y * L * a.m;
-  time_body<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD>(in + rb, out + rb, a, tb, blockIdx.x);
+  time_body<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD, OTF>(in + rb, out + rb, a, tb, blockIdx.x);
 }
 
 // Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.
 template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false,
-          int PRELOAD = 0>
+          int PRELOAD = 0, bool OTF = false>
 static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
   constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
@@ -275,7 +325,7 @@ static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int n
   a.m = P.m;
   a.n = P.n;
   a.npairs = P.npairs;
-  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD>;
+  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD, OTF>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
   kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
@@ -302,6 +352,9 @@ static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrh
     if (v == 19) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, false, 8>(P, in, out, nrhs, s);
     if (v == 20) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, false, 16>(P, in, out, nrhs, s);
     if (v == 21) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, false, 16>(P, in, out, nrhs, s);
+    // 22, 23 = 18, 19 with the spectral table slice computed on the fly
+    if (v == 22) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, false, 8, true>(P, in, out, nrhs, s);
+    if (v == 23) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, false, 8, true>(P, in, out, nrhs, s);
   }
   if constexpr (std::is_same<R, dfl>::value) {
     // 12, 13 = variants 9, 11 with the loads batched 8 tasks at a time
