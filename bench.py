@@ -101,11 +101,11 @@ def algorithmic_flops(cls: str, d: int, N: int, nt: int, unknowns: int, varcoef:
         # where the operator is Lambda (v_i + v_{i-2}) - 2 v_{i-1} (4 flops); the
         # physical residual check applies the stencil L (2d neighbours summed, scaled
         # and subtracted from the scaled centre: 2d + 2) and the time band (3).  The
-        # variable-coefficient L, written as a weighted sum of the centre and its 2d
-        # neighbours with time-invariant weights, takes one product and 2d multiply-adds
-        # (4d + 1) per application, plus the time band.  A fused dot adds 2, a residual 3.
+        # variable-coefficient L, the centre plus 2d face-weighted differences with
+        # time-invariant weights, takes a difference and a multiply-add per face (6d)
+        # per application, plus the time band.  A fused dot adds 2, a residual 3.
         if varcoef:
-            op = 4 * d + 4
+            op = 6 * d + 3
         elif cls == "yt_res":
             op = 2 * d + 5
         else:
@@ -926,7 +926,7 @@ def run_profile_case(args):
             torch.cuda.synchronize()
         print("ok")
         return 0
-    nvar = {"fp64": 8, "fp32": 24, "f32x2": 14}[args.precision]
+    nvar = {"fp64": 8, "fp32": 30, "f32x2": 14}[args.precision]
     times = {}
     for v in range(nvar):
         os.environ["AAO_TIME_VARIANT"] = f"{v},{v},{v}"

@@ -341,8 +341,9 @@ const char* aao_serve_last_error(void);
  * 2048/n mode pairs per CTA; shared-memory layout: sequence-major or interleaved and
  * padded, the latter with or without a staged slice of the spectral table; and, for
  * the FP32 and double-float pipelines on FP64 vectors, loads batched ahead of their
- * conversion, bulk-copy staging of the tile or integer conversions, and, in FP32, the
- * spectral table read from memory or computed on the fly) and of the DST
+ * conversion, bulk-copy staging of the tile or integer conversions (of the loads, the
+ * stores or both), and, in FP32, the spectral table read from memory or computed on
+ * the fly) and of the DST
  * kernel (radix-4 or radix-16 stage plan, with or without batched loads) by timing
  * each on the handle's workspace with CUDA events (the work of the kernels is
  * the same in every variant; only speed differs).  The default variant is kept unless

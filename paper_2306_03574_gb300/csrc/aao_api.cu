@@ -1317,8 +1317,9 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // 12, 13: 9 and 11 with batched loads), the FP32 pipeline on FP64 vectors sixteen
   // (8..15: the tile staged by bulk copies; 16, 17: variants 5 and 7 with integer
   // conversions; 18..21: with batched loads; 22, 23: 18, 19 with the spectral table
-  // computed on the fly instead of read)
-  const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 24 : 8;
+  // computed on the fly instead of read; 24..29: 18, 19 with the store, load or both
+  // conversions by integer operations)
+  const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 30 : 8;
   std::vector<float> tt(ntv), td(4);
   for (int v = 0; v < ntv; ++v) {
     tvar(P, prec) = v;

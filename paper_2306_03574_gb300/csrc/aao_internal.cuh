@@ -72,7 +72,7 @@ struct Plan {
   // GB300: FP64 (FP64-pipe bound) radix-16 + half tile; FP32 on FP64 vectors variant 5
   // (radix-16, full tile, interleaved) with batched loads; double-float radix-16, full
   // tile, interleaved without the staged table, with batched loads.
-  int time_variant64 = 3, time_variant32 = 18, time_variant_ff = 12;
+  int time_variant64 = 3, time_variant32 = 24, time_variant_ff = 12;
   // DST variant: bit 0 = radix-16-first stage plan (else radix-4), bit 1 = batched
   // pre-processing loads (aao_create: 1 for FP64 handles, 3 otherwise)
   int dst_variant = 1;

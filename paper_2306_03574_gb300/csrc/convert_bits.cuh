@@ -44,16 +44,19 @@ __device__ __forceinline__ double to_f64(float x) {
 }
 
 
-// load / store conversion of a kernel that computes in R on vectors of TIO
-template <typename R, typename TIO, bool ICVT>
+// load / store conversion of a kernel that computes in R on vectors of TIO.  CVM (FP32
+// on FP64 vectors only): bit 0 converts the loads, bit 1 the stores by integer
+// operations; the others stay cvt instructions.  Splitting them spreads the conversions
+// over the FP64 pipe and the integer units.
+template <typename R, typename TIO, int CVM>
 struct Cvt {
   static __device__ __forceinline__ R load(TIO x) { return R(x); }
   static __device__ __forceinline__ TIO store(R x) { return TIO(x); }
 };
-template <>
-struct Cvt<float, double, true> {
-  static __device__ __forceinline__ float load(double x) { return d2f_bits(x); }
-  static __device__ __forceinline__ double store(float x) { return f2d_bits(x); }
+template <int CVM>
+struct Cvt<float, double, CVM> {
+  static __device__ __forceinline__ float load(double x) { return to_f32<(CVM & 1) != 0>(x); }
+  static __device__ __forceinline__ double store(float x) { return to_f64<(CVM & 2) != 0>(x); }
 };
 
 }  // namespace aao

@@ -275,30 +275,47 @@ __device__ __forceinline__ Faces load_faces(int ix, int iy, int iz, const VarArg
   return f;
 }
 
+// L_a w(s) = w(s) + sum_faces g (w(s) - w(neighbour)) with g = cv a per face, the
+// neighbour outside the grid 0.  The g are constant in time, so a thread forms them once
+// for its run: each application is one difference and one multiply-add per face (the
+// FP64 pipe bounds this kernel).  The differences are kept rather than expanding to
+// (1 + sum g) w(s) - sum g w(neighbour): with a ~ 10^3 that form cancels three digits.
+struct VarStencil {
+  double xl, xr, yl, yr, zl, zr;
+};
+
+template <int D>
+__device__ __forceinline__ VarStencil var_stencil(const Faces& f, double cv) {
+  VarStencil g{};
+  g.xl = cv * f.xl;
+  g.xr = cv * f.xr;
+  if (D >= 2) { g.yl = cv * f.yl; g.yr = cv * f.yr; }
+  if (D >= 3) { g.zl = cv * f.zl; g.zr = cv * f.zr; }
+  return g;
+}
+
 template <int D>
 __device__ __forceinline__ double apply_La_f(const double* __restrict__ v, int s, int ix, int iy, int iz, int N,
-                                             double cv, const Faces& f) {
+                                             const VarStencil& g) {
   const double c = v[s];
-  double acc;
-  {
-    const double wl = ix > 0 ? v[s - 1] : 0.0, wr = ix < N - 1 ? v[s + 1] : 0.0;
-    acc = fma(f.xr, c - wr, f.xl * (c - wl));
-  }
+  double acc = c;
+  acc = fma(g.xl, c - (ix > 0 ? v[s - 1] : 0.0), acc);
+  acc = fma(g.xr, c - (ix < N - 1 ? v[s + 1] : 0.0), acc);
   if (D >= 2) {
-    const double wl = iy > 0 ? v[s - N] : 0.0, wr = iy < N - 1 ? v[s + N] : 0.0;
-    acc = fma(f.yr, c - wr, fma(f.yl, c - wl, acc));
+    acc = fma(g.yl, c - (iy > 0 ? v[s - N] : 0.0), acc);
+    acc = fma(g.yr, c - (iy < N - 1 ? v[s + N] : 0.0), acc);
   }
   if (D >= 3) {
-    const double wl = iz > 0 ? v[s - N * N] : 0.0, wr = iz < N - 1 ? v[s + N * N] : 0.0;
-    acc = fma(f.zr, c - wr, fma(f.zl, c - wl, acc));
+    acc = fma(g.zl, c - (iz > 0 ? v[s - N * N] : 0.0), acc);
+    acc = fma(g.zr, c - (iz < N - 1 ? v[s + N * N] : 0.0), acc);
   }
-  return fma(cv, acc, c);
+  return acc;
 }
 
 template <int D>
 __device__ __forceinline__ double apply_La(const double* __restrict__ v, int s, int ix, int iy, int iz,
                                            const VarArgs& a) {
-  return apply_La_f<D>(v, s, ix, iy, iz, a.N, a.cv, load_faces<D>(ix, iy, iz, a));
+  return apply_La_f<D>(v, s, ix, iy, iz, a.N, var_stencil<D>(load_faces<D>(ix, iy, iz, a), a.cv));
 }
 
 template <int D, int MODE>
@@ -316,11 +333,11 @@ __global__ void __launch_bounds__(YT_NT) k_yt_var(const double* __restrict__ x, 
     const int iy = (D >= 2) ? (s / N) % N : 0;
     const int iz = (D >= 3) ? s / (N * N) : 0;
     const double* xr = x + rb;
-    const Faces fc = load_faces<D>(ix, iy, iz, a);
+    const VarStencil g = var_stencil<D>(load_faces<D>(ix, iy, iz, a), a.cv);
     double Lv1 = 0.0, Lv2 = 0.0, v1 = 0.0;
     for (int i = max(0, i0 - 2); i < i1; ++i) {
       const double* vi = xr + (long long)i * m;
-      const double Lv = apply_La_f<D>(vi, s, ix, iy, iz, N, a.cv, fc);
+      const double Lv = apply_La_f<D>(vi, s, ix, iy, iz, N, g);
       if (i >= i0) {
         const double o = fma(-2.0, v1, Lv + Lv2);
         const long long idx = rb + (long long)(n - 1 - i) * m + s;

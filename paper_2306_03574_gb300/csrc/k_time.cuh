@@ -178,13 +178,13 @@ template <int L> struct FoldScaling<double, L> { static constexpr bool value = t
 template <int L> struct FoldScaling<float, L> { static constexpr bool value = L <= 256; };
 
 // Tile `tile` (mode pairs tile*NS ..) of one right-hand side: in and out point at it.
-// ICVT: FP64 <-> FP32 conversions of the load and store by integer operations
-// (convert_bits.cuh) instead of cvt instructions on the FP64 pipe.
+// ICVT: FP64 <-> FP32 conversions by integer operations (convert_bits.cuh) instead of
+// cvt instructions on the FP64 pipe: bit 0 those of the loads, bit 1 those of the stores.
 // PRELOAD > 0: the tile's loads batched in registers, PRELOAD tasks (two values each)
 // per batch, every load of a batch issued before the first is converted.
 // OTF (FP32 with PRELOAD and the staged layout): the table slice computed on the fly
 // (compute_table) while the first batch of loads is in flight, instead of read.
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG, bool ICVT = false,
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG, int ICVT = 0,
           int PRELOAD = 0, bool OTF = false>
 __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArgs& a, const PrecTables<R>& tb,
                                           int tile) {
@@ -306,7 +306,7 @@ __device__ __forceinline__ void time_body(const TIO* in, TIO* out, const TimeArg
   }
 }
 
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false,
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, int ICVT = 0,
           int PRELOAD = 0, bool OTF = false>
 __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
   const long long rb = (long long)blockIdx.y * L * a.m;
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
 }
 
 // Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.
-template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, bool ICVT = false,
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, int ICVT = 0,
           int PRELOAD = 0, bool OTF = false>
 static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
@@ -346,20 +346,28 @@ static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrh
   if constexpr (std::is_same<R, float>::value && std::is_same<TIO, double>::value) {
     // FP32 arithmetic on FP64 vectors: 16, 17 = variants 5, 7 with integer conversions;
     // 18, 19 = variants 5, 7 with the loads batched 8 tasks at a time, 20, 21 16 at a time
-    if (v == 16) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, true>(P, in, out, nrhs, s);
-    if (v == 17) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, true>(P, in, out, nrhs, s);
-    if (v == 18) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, false, 8>(P, in, out, nrhs, s);
-    if (v == 19) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, false, 8>(P, in, out, nrhs, s);
-    if (v == 20) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, false, 16>(P, in, out, nrhs, s);
-    if (v == 21) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, false, 16>(P, in, out, nrhs, s);
+    if (v == 16) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, 3>(P, in, out, nrhs, s);
+    if (v == 17) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 3>(P, in, out, nrhs, s);
+    if (v == 18) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, 0, 8>(P, in, out, nrhs, s);
+    if (v == 19) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 0, 8>(P, in, out, nrhs, s);
+    if (v == 20) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, 0, 16>(P, in, out, nrhs, s);
+    if (v == 21) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 0, 16>(P, in, out, nrhs, s);
     // 22, 23 = 18, 19 with the spectral table slice computed on the fly
-    if (v == 22) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, false, 8, true>(P, in, out, nrhs, s);
-    if (v == 23) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, false, 8, true>(P, in, out, nrhs, s);
+    if (v == 22) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, 0, 8, true>(P, in, out, nrhs, s);
+    if (v == 23) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 0, 8, true>(P, in, out, nrhs, s);
+    // 24, 25 = 18, 19 with the stores converted by integer operations; 26, 27 the loads;
+    // 28, 29 both
+    if (v == 24) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, 2, 8>(P, in, out, nrhs, s);
+    if (v == 25) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 2, 8>(P, in, out, nrhs, s);
+    if (v == 26) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, 1, 8>(P, in, out, nrhs, s);
+    if (v == 27) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 1, 8>(P, in, out, nrhs, s);
+    if (v == 28) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, 3, 8>(P, in, out, nrhs, s);
+    if (v == 29) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 3, 8>(P, in, out, nrhs, s);
   }
   if constexpr (std::is_same<R, dfl>::value) {
     // 12, 13 = variants 9, 11 with the loads batched 8 tasks at a time
-    if (v == 12) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, 0, false, 8>(P, in, out, nrhs, s);
-    if (v == 13) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, 0, false, 8>(P, in, out, nrhs, s);
+    if (v == 12) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, 0, 0, 8>(P, in, out, nrhs, s);
+    if (v == 13) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, 0, 0, 8>(P, in, out, nrhs, s);
     if (v & 8) {  // interleaved layout without the staged table slice
       switch (v & 3) {
         case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0, 1, 0>(P, in, out, nrhs, s);

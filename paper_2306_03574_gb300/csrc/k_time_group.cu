@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(NT) k_g_time(const TimeGroup<R>* __restrict__ 
   a.m = e.m;
   a.n = L;
   a.npairs = e.npairs;
-  time_body<R, double, L, NS, NT, FFTV, LAY, STG, false, PRE>(e.in, e.out, a, e.tb, blockIdx.x - g->tile[r]);
+  time_body<R, double, L, NS, NT, FFTV, LAY, STG, 0, PRE>(e.in, e.out, a, e.tb, blockIdx.x - g->tile[r]);
 }
 
 // The variant of each precision that has a grouped form -- the precision's default --

@@ -57,8 +57,9 @@ def test_time_variants(d, N, nt, monkeypatch):
     tol64 = gates.fp64("time", d, N, nt, ALPHA)
     outs = []
     # FP32 on FP64 vectors: 8..15 bulk-staged tile, 16, 17 integer conversions, 18..21
-    # loads batched ahead of their conversion, 22, 23 spectral table computed on the fly
-    for v in range(24):
+    # loads batched ahead of their conversion, 22, 23 spectral table computed on the fly,
+    # 24..29 batched loads with integer conversions of the stores, the loads or both
+    for v in range(30):
         monkeypatch.setenv("AAO_TIME_VARIANT", f"{v & 7},{v}")
         for prec in (aao.AAO_PREC_FP64, aao.AAO_PREC_FP32_IR) if v < 8 else (aao.AAO_PREC_FP32_IR,):
             with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=prec) as s:
@@ -80,7 +81,7 @@ def test_time_variants(d, N, nt, monkeypatch):
 
 @pytest.mark.parametrize("d,N,nt", [(2, 63, 64), (1, 255, 256), (1, 511, 512), (2, 127, 128)])
 def test_bulk_staged_time_kernel_guards_and_alignment(d, N, nt, monkeypatch):
-    """The bulk-staged FP32 kernels (variants 8..15) and the batched-load ones (18..23)
+    """The bulk-staged FP32 kernels (variants 8..15) and the batched-load ones (18..29)
     write nothing outside their output
     (guard bands at both ends), and a vector that is only 8-byte aligned -- which bulk
     copies cannot address -- is served by the register-staged variant with the same
@@ -90,7 +91,7 @@ def test_bulk_staged_time_kernel_guards_and_alignment(d, N, nt, monkeypatch):
     x = W.random_field((nt, m), seed=1750 + nt + N)
     ref = _time_ref(d, N, nt, x)
     tol32 = gates.fp32("time", d, N, nt, ALPHA)
-    for v in list(range(8, 16)) + [18, 19, 20, 21, 22, 23]:
+    for v in list(range(8, 16)) + list(range(18, 30)):
         monkeypatch.setenv("AAO_TIME_VARIANT", f"3,{v}")
         with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=aao.AAO_PREC_FP32_IR) as s:
             xt = guards.guarded_copy(x)
