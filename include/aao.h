@@ -127,7 +127,10 @@ typedef struct aao_handle aao_handle;
  *   AAO_TIME_VARIANT="v64[,v32[,vff]]" sets the time-kernel variant per precision
  *   (the numbering of aao_autotune; a missing entry repeats the previous one), and
  *   AAO_DST_VARIANT="0..3" the DST variant (bit 0: radix-16-first stage plan, bit 1:
- *   batched loads).  Every variant computes the same values.
+ *   batched loads), and AAO_FUSED_SCALARS=1 runs the MINRES scalar steps in the tails
+ *   of the kernels that produce their partial sums (five launches per iteration instead
+ *   of eight, and no separate loop-condition launch in a graph trip).  Every variant
+ *   computes the same values (bit for bit, for the fused scalar steps).
  * Errors: AAO_EINVAL, AAO_EUNSUPPORTED, AAO_ENOMEM, AAO_ECUDA, AAO_ESINGULAR. */
 aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha,
                       aao_scheme scheme, const aao_opts* opts, aao_handle** out);

@@ -103,6 +103,11 @@ struct aao_handle {
   double* partial = nullptr; int partial_stride = 0;  // 3 * nrhs_max * partial_stride
   MinresScalars* sc = nullptr;
   MinresScalars* sc_host = nullptr;  // pinned
+  // MINRES scalar steps fused into the kernels that produce their partial sums (off unless
+  // AAO_FUSED_SCALARS=1: on GB300 the serial tail costs about what the graph node it
+  // removes costs); arrive: their arrival counters [nrhs_max + 1], zero between launches
+  bool fuse_scalars = false;
+  unsigned* arrive = nullptr;
   // host-solve staging (allocated on first aao_solve_host)
   double* hs_f = nullptr; double* hs_psi = nullptr; double* hs_b = nullptr; double* hs_x = nullptr;
   cudaStream_t hs_copy = nullptr;    // copy stream of the pipelined host-buffer solve
@@ -348,9 +353,9 @@ aao_status dst_apply_levels(aao_handle* h, const double* in, double* out, int nl
 
 // The physical operator Y T (constant or variable coefficient), modes as launch_yt.
 cudaError_t launch_op(aao_handle* h, const double* x, double* y, const double* w, double* partial, int mode,
-                      int nrhs, cudaStream_t s, int* nb) {
-  if (h->var_on) return launch_yt_var(h->P, h->face, x, y, w, partial, mode, nrhs, s, &h->launches, nb);
-  return launch_yt(h->P, x, y, w, partial, mode, nrhs, s, &h->launches, nb);
+                      int nrhs, cudaStream_t s, int* nb, const ScalarTail* tail = nullptr) {
+  if (h->var_on) return launch_yt_var(h->P, h->face, x, y, w, partial, mode, nrhs, s, &h->launches, nb, tail);
+  return launch_yt(h->P, x, y, w, partial, mode, nrhs, s, &h->launches, nb, tail);
 }
 
 cudaError_t launch_rhs(aao_handle* h, const double* f, const double* psi0, const double* psi1, double* b,
@@ -379,9 +384,14 @@ struct MinresCtx {
   cudaStream_t s;
   bool true_res, physical;
   const double* prm = nullptr;  // graph capture: rtol, maxit read from device memory
-  cudaError_t op(const double* xx, double* yy, const double* ww, double* part, int mode, int* nbp) const {
-    return physical ? launch_op(h, xx, yy, ww, part, mode, nrhs, s, nbp)
-                    : launch_ythat(h->P, h->lam64, xx, yy, ww, part, mode, nrhs, s, &h->launches, nbp);
+  // graph capture: the WHILE condition handle and the trip limit of the loop body
+  bool in_graph = false;
+  cudaGraphConditionalHandle hw = 0;
+  int trip_limit = 0;
+  cudaError_t op(const double* xx, double* yy, const double* ww, double* part, int mode, int* nbp,
+                 const ScalarTail* tail = nullptr) const {
+    return physical ? launch_op(h, xx, yy, ww, part, mode, nrhs, s, nbp, tail)
+                    : launch_ythat(h->P, h->lam64, xx, yy, ww, part, mode, nrhs, s, &h->launches, nbp, tail);
   }
   aao_status prec(const double* in, double* out) const {
     return physical ? prec_apply(h, in, out, nrhs, s) : time_apply(h, in, out, nrhs, s);
@@ -423,8 +433,13 @@ aao_status minres_enqueue_init(const MinresCtx& c, int use_x0, const MinresBufs&
 }
 
 // One MINRES iteration with buffers B (stream-ordered, no host synchronisation);
-// afterwards the roles rotate: (v, vp), (z, zn), (w, wp) swap.
-aao_status minres_enqueue_iter(const MinresCtx& c, const MinresBufs& B) {
+// afterwards the roles rotate: (v, vp), (z, zn), (w, wp) swap.  With fused scalar steps
+// (h->fuse_scalars) each step runs in the tail of the kernel that produces its partial
+// sums, with the same code and summation order as k_scalars (same bits), and an
+// iteration is five launches in the DST basis: operator + delta, v update,
+// preconditioner, dot + gamma/Givens, w/x update + residual + stop test.  ends_trip (graph
+// capture): this iteration's stop test also sets the loop condition (no k_loop_cond).
+aao_status minres_enqueue_iter(const MinresCtx& c, const MinresBufs& B, bool ends_trip = false) {
   aao_handle* h = c.h;
   const Plan& P = h->P;
   const cudaStream_t s = c.s;
@@ -432,26 +447,48 @@ aao_status minres_enqueue_iter(const MinresCtx& c, const MinresBufs& B) {
   const int nb_dot = dot_blocks_per_rhs(P);
   uint64_t* nl = &h->launches;
   const int nrhs = c.nrhs;
+  const bool fz = h->fuse_scalars;
+  auto tail = [&](int step, bool cond) {
+    ScalarTail t;
+    t.sc = h->sc;
+    t.arrive = h->arrive;
+    t.step = step;
+    t.slot_all = h->nrhs_max;
+    t.nrhs = nrhs;
+    if (cond && c.in_graph) {
+      t.cond = 1;
+      t.hw = c.hw;
+      t.trips = h->d_trips;
+      t.trip_limit = c.trip_limit;
+      t.prm = c.prm;
+    }
+    return t;
+  };
+  auto scal = [&](int step, int nb) {
+    return launch_scalars(step, h->sc, p1, nb, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl);
+  };
+  const ScalarTail t1 = tail(1, false), t2 = tail(2, false), tl = tail(c.true_res ? 3 : 4, ends_trip);
   int nb_yt = 0;
-  AAO_KL(h, KC_YT_DOT, s, c.op(B.z, h->vT, B.z, p1, 1, &nb_yt));
-  AAO_KL(h, KC_SCAL, s, launch_scalars(1, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+  AAO_KL(h, KC_YT_DOT, s, c.op(B.z, h->vT, B.z, p1, 1, &nb_yt, fz ? &t1 : nullptr));
+  if (!fz) AAO_KL(h, KC_SCAL, s, scal(1, nb_yt));
   AAO_KL(h, KC_VUPD, s, launch_vupdate(P, h->vT, B.v, B.vp, h->sc, nrhs, s, nl));  // vp <- v_{j+1}
   AAO_TRY(c.prec(B.vp, B.zn));
-  AAO_KL(h, KC_DOT, s, launch_dot(P, B.zn, B.vp, p1, nrhs, s, nl));
-  AAO_KL(h, KC_SCAL, s, launch_scalars(2, h->sc, p1, nb_dot, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+  AAO_KL(h, KC_DOT, s, launch_dot(P, B.zn, B.vp, p1, nrhs, s, nl, fz ? &t2 : nullptr));
+  if (!fz) AAO_KL(h, KC_SCAL, s, scal(2, nb_dot));
   if (c.true_res && !c.physical) {
     // DST basis: the update and the true residual of the new iterate in one pass
     AAO_KL(h, KC_WXRES, s, launch_wx_res(P, h->lam64, B.z, B.wp, B.w, c.xh, c.bh, h->sc, p1, nrhs, s, nl,
-                                         &nb_yt));  // wp <- w_{j+1}
-    AAO_KL(h, KC_SCAL, s, launch_scalars(3, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+                                         &nb_yt, fz ? &tl : nullptr));  // wp <- w_{j+1}
+    if (!fz) AAO_KL(h, KC_SCAL, s, scal(3, nb_yt));
     return AAO_OK;
   }
-  AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, B.z, B.wp, B.w, c.xh, h->sc, nrhs, s, nl));  // wp <- w_{j+1}
   if (c.true_res) {
-    AAO_KL(h, KC_YT_RES, s, c.op(c.xh, nullptr, c.bh, p1, 2, &nb_yt));
-    AAO_KL(h, KC_SCAL, s, launch_scalars(3, h->sc, p1, nb_yt, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+    AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, B.z, B.wp, B.w, c.xh, h->sc, nrhs, s, nl));  // wp <- w_{j+1}
+    AAO_KL(h, KC_YT_RES, s, c.op(c.xh, nullptr, c.bh, p1, 2, &nb_yt, fz ? &tl : nullptr));
+    if (!fz) AAO_KL(h, KC_SCAL, s, scal(3, nb_yt));
   } else {
-    AAO_KL(h, KC_SCAL, s, launch_scalars(4, h->sc, p1, 0, nullptr, 0, nullptr, 0, nrhs, c.rtol, c.maxit, s, nl));
+    AAO_KL(h, KC_WXUPD, s, launch_wxupdate(P, B.z, B.wp, B.w, c.xh, h->sc, nrhs, s, nl, fz ? &tl : nullptr));
+    if (!fz) AAO_KL(h, KC_SCAL, s, scal(4, 0));
   }
   return AAO_OK;
 }
@@ -489,6 +526,8 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   cc.prm = h->d_prm;  // rtol and maxit are set before each launch, not captured
   const MinresBufs B0{h->vv, h->vvp, h->vz, h->vzn, h->vw, h->vwp};
   const int trip_limit = c.maxit / 2 + 2;
+  cc.in_graph = true;
+  cc.trip_limit = trip_limit;
   cudaGraph_t g = nullptr;
   AAO_CK(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle hw;
@@ -505,6 +544,7 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   };
   cudaError_t e = cudaGraphConditionalHandleCreate(&hw, g, 0, cudaGraphCondAssignDefault);
   if (e != cudaSuccess) return fail_cleanup(e, "cudaGraphConditionalHandleCreate");
+  cc.hw = hw;
   e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return fail_cleanup(e, "cudaStreamBeginCaptureToGraph");
   if (cudaMemsetAsync(h->d_trips, 0, sizeof(int), cs) != cudaSuccess ||
@@ -537,8 +577,10 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
   e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return fail_cleanup(e, "capture of the loop body");
   const MinresBufs B1 = rotate(B0);
-  if (minres_enqueue_iter(cc, B0) != AAO_OK || minres_enqueue_iter(cc, B1) != AAO_OK ||
-      launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 1, cs, &h->launches, h->d_prm) != cudaSuccess) {
+  // the second iteration's stop test sets the loop condition when the steps are fused
+  if (minres_enqueue_iter(cc, B0) != AAO_OK || minres_enqueue_iter(cc, B1, true) != AAO_OK ||
+      (!h->fuse_scalars &&
+       launch_loop_cond(hw, h->sc, c.nrhs, h->d_trips, trip_limit, 1, cs, &h->launches, h->d_prm) != cudaSuccess)) {
     h->launches = l0;
     return fail_cleanup(cudaGetLastError(), "loop body capture");
   }
@@ -911,6 +953,13 @@ aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double 
 aao_status aaoi_serving_prepare(aao_handle* h) {
   if (!h) return fail(AAO_EINVAL, "null handle");
   if (h->pin) return AAO_OK;
+  // served problems run their time pipelines in grouped launches, which take the
+  // standard tiles: a small problem keeps them too (its CTAs share the grouped grid)
+  Plan& Pm = h->P;
+  const Plan standard;
+  if (Pm.time_variant64 == TIME_VARIANT_SMALL) Pm.time_variant64 = standard.time_variant64;
+  if (Pm.time_variant32 == TIME_VARIANT_SMALL) Pm.time_variant32 = standard.time_variant32;
+  if (Pm.time_variant_ff == TIME_VARIANT_SMALL) Pm.time_variant_ff = standard.time_variant_ff;
   const Plan& P = h->P;
   const size_t nt = (size_t)P.n;
   const size_t bytes = 2 * nt * sizeof(double2) + 2 * nt * sizeof(double) + (size_t)P.m * sizeof(double) +
@@ -1070,6 +1119,14 @@ const char* aao_status_str(aao_status s) {
 
 const char* aao_last_error(void) { return g_err.c_str(); }
 
+// A time-kernel variant number of a precision mode, or the small-tile variant (any
+// other number is folded onto the range the mode has).
+static int clamp_time_variant(int v, int prec) {
+  if (v == TIME_VARIANT_SMALL) return v;
+  return v & (prec == AAO_PREC_FP64 ? 7 : prec == AAO_PREC_F32X2 ? 15 : 31);
+}
+static int clamp_dst_variant(int v) { return v == DST_VARIANT_SMALL ? v : v & 3; }
+
 aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aao_scheme scheme,
                       const aao_opts* opts, aao_handle** out) {
   g_err.clear();
@@ -1122,16 +1179,26 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   // DST default: the FP64 DST is bound by the FP64 pipe; the double-float and FP32 DSTs
   // (the handle's DSTs in the other modes) gain from batched loads (measured on GB300)
   P.dst_variant = o.precision == AAO_PREC_FP64 ? 1 : 3;
+  // Small problems: when even the half tile (2048/n mode pairs, 2048/(N+1) line pairs)
+  // gives fewer CTAs than a quarter of the 152 SMs, the one-warp small tiles spread the
+  // work wider (C1, 1D 63 x 64: 1 CTA -> 16).
+  if ((P.npairs + 2048 / nt - 1) / (2048 / nt) < 38) {
+    P.time_variant64 = P.time_variant32 = P.time_variant_ff = TIME_VARIANT_SMALL;
+  }
+  {
+    const long long lines = (long long)nt * P.m / P.N, ns = 2048 / M;
+    if ((lines + 2 * ns - 1) / (2 * ns) < 38) P.dst_variant = DST_VARIANT_SMALL;
+  }
   if (const char* tv = getenv("AAO_TIME_VARIANT")) {  // tuning override: "v64,v32,vff"
     int a = 0, b = -1;
     int c = -1;
     if (sscanf(tv, "%d,%d,%d", &a, &b, &c) >= 1) {
-      P.time_variant64 = a & 7;
-      P.time_variant32 = (b >= 0 ? b : a) & 31;
-      P.time_variant_ff = (c >= 0 ? c : (b >= 0 ? b : a)) & 15;
+      P.time_variant64 = clamp_time_variant(a, AAO_PREC_FP64);
+      P.time_variant32 = clamp_time_variant(b >= 0 ? b : a, AAO_PREC_FP32_IR);
+      P.time_variant_ff = clamp_time_variant(c >= 0 ? c : (b >= 0 ? b : a), AAO_PREC_F32X2);
     }
   }
-  if (const char* dv = getenv("AAO_DST_VARIANT")) P.dst_variant = atoi(dv) & 3;
+  if (const char* dv = getenv("AAO_DST_VARIANT")) P.dst_variant = clamp_dst_variant(atoi(dv));
 
   auto bail = [&](aao_status st) { delete h; return st; };
 
@@ -1210,8 +1277,9 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   if (o.host_staging && (st = reserve_host_staging(h))) return bail(st);
   h->partial_stride = std::max(std::max(yt_blocks_per_rhs(P), dot_blocks_per_rhs(P)), wxres_blocks_per_rhs(P));
   if ((st = h->alloc(&h->partial, (size_t)3 * h->nrhs_max * h->partial_stride)) ||
-      (st = h->alloc(&h->sc, (size_t)h->nrhs_max)))
+      (st = h->alloc(&h->sc, (size_t)h->nrhs_max)) || (st = h->alloc(&h->arrive, (size_t)h->nrhs_max + 1)))
     return bail(st);
+  if (const char* fz = getenv("AAO_FUSED_SCALARS")) h->fuse_scalars = atoi(fz) != 0;
   if (cudaMallocHost(&h->sc_host, sizeof(MinresScalars) * h->nrhs_max) != cudaSuccess ||
       cudaMallocHost(&h->relres_host, sizeof(double) * h->nrhs_max) != cudaSuccess) {
     cudaGetLastError();
@@ -1220,6 +1288,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
 
   auto run = [&]() -> aao_status {
     const cudaStream_t os = h->own_stream;
+    AAO_CK(cudaMemsetAsync(h->arrive, 0, ((size_t)h->nrhs_max + 1) * sizeof(unsigned), os));
     AAO_TRY(upload_on(twS, h->tw_space64, os));
     AAO_TRY(upload_on(sinw, h->sinw64, os));
     AAO_TRY(upload_on(twT, h->tw_time64, os));
@@ -1274,8 +1343,8 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
       bool found = false;
       while (fscanf(fh, "%d %d %d %d %d %d", &d, &N, &n, &pr, &tv, &dv) == 6)
         if (d == P.d && N == P.N && n == P.n && pr == prec) {
-          tvar(P, prec) = tv & (prec == AAO_PREC_FP64 ? 7 : 31);
-          P.dst_variant = dv & 3;
+          tvar(P, prec) = clamp_time_variant(tv, prec);
+          P.dst_variant = clamp_dst_variant(dv);
           found = true;
         }
       fclose(fh);
@@ -1319,32 +1388,38 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // conversions; 18..21: with batched loads; 22, 23: 18, 19 with the spectral table
   // computed on the fly instead of read; 24..29: 18, 19 with the store, load or both
   // conversions by integer operations)
+  // conversions by integer operations); every mode also has the small tile
   const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 30 : 8;
-  std::vector<float> tt(ntv), td(4);
-  for (int v = 0; v < ntv; ++v) {
-    tvar(P, prec) = v;
-    tt[v] = timeit([&]() {
+  std::vector<int> tvs, dvs = {0, 1, 2, 3, DST_VARIANT_SMALL};
+  for (int v = 0; v < ntv; ++v) tvs.push_back(v);
+  tvs.push_back(TIME_VARIANT_SMALL);
+  auto pick = [](const std::vector<int>& vs, const std::vector<float>& t, int def) {
+    size_t b = 0, d = 0;
+    for (size_t i = 0; i < vs.size(); ++i) {
+      if (t[i] < t[b]) b = i;
+      if (vs[i] == def) d = i;
+    }
+    return t[b] < 0.99f * t[d] ? vs[b] : def;
+  };
+  std::vector<float> tt(tvs.size()), td(dvs.size());
+  for (size_t i = 0; i < tvs.size(); ++i) {
+    tvar(P, prec) = tvs[i];
+    tt[i] = timeit([&]() {
       if (prec == AAO_PREC_FP64) launch_time<double>(P, h->vv, h->vz, 1, s, nullptr);
       else if (prec == AAO_PREC_F32X2) launch_time_ff(P, h->vv, h->vz, 1, s, nullptr);
       else launch_time_mixed(P, h->vv, h->vz, 1, s, nullptr);
     });
   }
-  int best_tv = 0;
-  for (int v = 1; v < ntv; ++v)
-    if (tt[v] < tt[best_tv]) best_tv = v;
-  if (!(tt[best_tv] < 0.99f * tt[def_tv])) best_tv = def_tv;
+  const int best_tv = pick(tvs, tt, def_tv);
   tvar(P, prec) = best_tv;
-  for (int v = 0; v < 4; ++v) {
-    P.dst_variant = v;
-    td[v] = timeit([&]() {
+  for (size_t i = 0; i < dvs.size(); ++i) {
+    P.dst_variant = dvs[i];
+    td[i] = timeit([&]() {
       if (prec == AAO_PREC_F32X2 || prec == AAO_PREC_FP32_IR) launch_dst_axis_ff(P, h->vv, h->vz, 0, 1, s, nullptr);
       else launch_dst_axis<double>(P, h->vv, h->vz, 0, 1, s, nullptr);
     });
   }
-  int best_dv = 0;
-  for (int v = 1; v < 4; ++v)
-    if (td[v] < td[best_dv]) best_dv = v;
-  if (!(td[best_dv] < 0.99f * td[def_dv])) best_dv = def_dv;
+  const int best_dv = pick(dvs, td, def_dv);
   P.dst_variant = best_dv;
   if (chosen) {
     chosen[0] = best_tv;

@@ -61,6 +61,14 @@ struct PrecTables {
   R inv2n = 0;                  // 1/(2n)
 };
 
+// Small-problem tiles: one warp per CTA and the fewest mode pairs (time pipeline) or
+// line pairs (DST) the radix-4 stage plan allows (128/L, at least 1), so that a problem
+// of a few thousand unknowns spreads over tens of SMs instead of one CTA.
+constexpr int TIME_VARIANT_SMALL = 30;
+constexpr int DST_VARIANT_SMALL = 4;
+constexpr int SMALL_NT = 32;
+constexpr int small_pairs(int L) { return L >= 128 ? 1 : 128 / L; }
+
 struct Plan {
   int d = 0, N = 0, M = 0, n = 0, m = 0, npairs = 0;
   double tau = 0, alpha = 0, c2 = 0, h = 0;
@@ -70,11 +78,14 @@ struct Plan {
   // the table slice staged in shared memory; higher numbers add batched loads, bulk-copy
   // staging or integer conversions (k_time.cuh, k_time32.cu).  Defaults measured on
   // GB300: FP64 (FP64-pipe bound) radix-16 + half tile; FP32 on FP64 vectors variant 5
-  // (radix-16, full tile, interleaved) with batched loads; double-float radix-16, full
-  // tile, interleaved without the staged table, with batched loads.
+  // (radix-16, full tile, interleaved) with batched loads and integer store
+  // conversions; double-float radix-16, full tile, interleaved without the staged table,
+  // with batched loads.  Every precision also has TIME_VARIANT_SMALL (aao_create's
+  // default when the standard tiles would leave most SMs idle).
   int time_variant64 = 3, time_variant32 = 24, time_variant_ff = 12;
   // DST variant: bit 0 = radix-16-first stage plan (else radix-4), bit 1 = batched
-  // pre-processing loads (aao_create: 1 for FP64 handles, 3 otherwise)
+  // pre-processing loads (aao_create: 1 for FP64 handles, 3 otherwise), or
+  // DST_VARIANT_SMALL
   int dst_variant = 1;
   PrecTables<double> t64;
   PrecTables<float> t32;
@@ -97,16 +108,20 @@ cudaError_t launch_dst_axis(const Plan& P, const R* in, R* out, int axis, int nr
 template <typename R>
 cudaError_t launch_time(const Plan& P, const R* in, R* out, int nrhs, cudaStream_t s, uint64_t* nl);
 
+struct ScalarTail;
 // Stencil kernels.  mode 0: y = Y T x.  mode 1: y = Y T x and partial[b] = sum y*w.
 // mode 2: no y; partial[b] = sum (w - Y T x)^2  (w = b, the true residual).
-// Partials are laid out [rhs][blocks_per_rhs]; returns blocks per rhs in *nb.
+// Partials are laid out [rhs][blocks_per_rhs]; returns blocks per rhs in *nb.  tail
+// (modes 1, 2; may be null): a MINRES scalar step run on the partials by the kernel.
 cudaError_t launch_yt(const Plan& P, const double* x, double* y, const double* w, double* partial,
-                      int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
+                      int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb,
+                      const ScalarTail* tail = nullptr);
 int yt_blocks_per_rhs(const Plan& P);
 // The operator in the DST basis (L -> diag(lam)); same modes and partial layout as launch_yt,
 // plus mode 3: y = w - Y T^ x written out, partials of ||y||^2.
 cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, double* y, const double* w,
-                         double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
+                         double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb,
+                         const ScalarTail* tail = nullptr);
 // Time pipeline computed in FP32/complex64 on FP64 vectors (conversion in the load and store).
 cudaError_t launch_time_mixed(const Plan& P, const double* in, double* out, int nrhs, cudaStream_t s,
                               uint64_t* nl);
@@ -127,7 +142,8 @@ cudaError_t launch_build_rhs_levels(const Plan& P, const double* f, const double
                                     double* b, int k0, int cnt, cudaStream_t s, uint64_t* nl);
 // Variable coefficient (face arrays, see aao_set_coefficient): operator and right-hand side.
 cudaError_t launch_yt_var(const Plan& P, const double* face, const double* x, double* y, const double* w,
-                          double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
+                          double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb,
+                          const ScalarTail* tail = nullptr);
 cudaError_t launch_build_rhs_var(const Plan& P, const double* face, const double* f, const double* psi0,
                                  const double* psi1, double* b, int nrhs, cudaStream_t s, uint64_t* nl);
 
@@ -147,21 +163,40 @@ struct MinresScalars {
   int iters, maxit, done, status;
 };
 
+// A MINRES scalar step fused into the tail of the kernel that produces its partial sums
+// (minres_scalars.cuh): the last block of each right-hand side to finish runs the step.
+// sc == nullptr: no fused step (the caller launches k_scalars).
+struct ScalarTail {
+  MinresScalars* sc = nullptr;
+  unsigned* arrive = nullptr;  // arrival counters [slot_all + 1], zero between launches
+  int step = 0;
+  int slot_all = 0;            // the counter over right-hand sides (cond)
+  int nrhs = 0;
+  // with cond: the last right-hand side to finish also sets the WHILE condition of the
+  // graph-captured solve (one loop trip; as k_loop_cond)
+  int cond = 0;
+  cudaGraphConditionalHandle hw = 0;
+  int* trips = nullptr;
+  int trip_limit = 0;
+  const double* prm = nullptr;
+};
+
 int dot_blocks_per_rhs(const Plan& P);
 // partial[rhs*nb + b] = sum_i a_i*c_i over the rhs's n*m entries
 cudaError_t launch_dot(const Plan& P, const double* a, const double* c, double* partial, int nrhs,
-                       cudaStream_t s, uint64_t* nl);
+                       cudaStream_t s, uint64_t* nl, const ScalarTail* tail = nullptr);
 // y = a0*x0 + a1*x1 + a2*x2 with coefficients sc[rhs].cv (which = 0) ; x2 may be null
 cudaError_t launch_vupdate(const Plan& P, const double* T, const double* v, double* vprev_out,
                            const MinresScalars* sc, int nrhs, cudaStream_t s, uint64_t* nl);
 cudaError_t launch_wxupdate(const Plan& P, const double* z, double* wprev_out, const double* w,
                             double* x, const MinresScalars* sc, int nrhs, cudaStream_t s,
-                            uint64_t* nl);
+                            uint64_t* nl, const ScalarTail* tail = nullptr);
 // launch_wxupdate fused with the true residual ||b - Y T^ x||^2 of the updated x in the DST
 // basis (partials [rhs][wxres_blocks_per_rhs], *nb = blocks per rhs); sc.done rhs untouched.
 cudaError_t launch_wx_res(const Plan& P, const double* lam, const double* z, double* wprev_out,
                           const double* w, double* x, const double* b, const MinresScalars* sc,
-                          double* partial, int nrhs, cudaStream_t s, uint64_t* nl, int* nb);
+                          double* partial, int nrhs, cudaStream_t s, uint64_t* nl, int* nb,
+                          const ScalarTail* tail = nullptr);
 int wxres_blocks_per_rhs(const Plan& P);
 // y = x0 - x1 (used for r0 = b - A x0)
 cudaError_t launch_sub(const Plan& P, const double* a, const double* b, double* y, int nrhs,

@@ -216,12 +216,11 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
   }
 }
 
-template <typename R, typename TIO, int M, int FFTV, bool PRE>
+// NS line pairs per CTA of NT threads (standard: 2048/M pairs, 128 threads)
+template <typename R, typename TIO, int M, int FFTV, bool PRE, int NS = 2048 / M, int NT = 128>
 static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs,
                                  cudaStream_t s) {
   using C = typename Cplx<R>::T;
-  constexpr int NT = 128;
-  constexpr int NS = 2048 / M;
   const PrecTables<R>& tb = tables<R>(P);
   const size_t smem = sizeof(C) * (NS * M + M) + sizeof(R) * (M / 2 + 1);
   DstArgs a;
@@ -252,7 +251,10 @@ static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axi
 template <typename R, typename TIO, int M>
 static cudaError_t dst_launch_M(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs,
                                 cudaStream_t s) {
-  // bit 0: radix-16 stage plan; bit 1: batched pre-processing loads
+  // bit 0: radix-16 stage plan; bit 1: batched pre-processing loads; or the small tile
+  // (one warp, small_pairs(M) line pairs, radix-4 plan)
+  if (P.dst_variant == DST_VARIANT_SMALL)
+    return dst_launch_MV<R, TIO, M, 0, false, small_pairs(M), SMALL_NT>(P, in, out, axis, nrhs, s);
   switch (P.dst_variant & 3) {
     case 0: return dst_launch_MV<R, TIO, M, 0, false>(P, in, out, axis, nrhs, s);
     case 1: return dst_launch_MV<R, TIO, M, 1, false>(P, in, out, axis, nrhs, s);

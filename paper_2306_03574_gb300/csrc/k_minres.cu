@@ -14,6 +14,7 @@
 // Every reduction is two-level and deterministic: fixed blocks write partial
 // sums, one warp per right-hand side adds them in a fixed order.
 #include "aao_internal.cuh"
+#include "minres_scalars.cuh"
 
 namespace aao {
 
@@ -53,6 +54,16 @@ __global__ void __launch_bounds__(VNT) k_dot(const double* __restrict__ a, const
   dot_body(a + rb, c + rb, partial + (long long)blockIdx.y * gridDim.x + blockIdx.x, len, blockIdx.x, gridDim.x);
 }
 
+// with a MINRES scalar step on the partials in the tail (minres_scalars.cuh); 8 resident
+// blocks per SM, the register budget of k_dot
+__global__ void __launch_bounds__(VNT, 8) k_dot_tail(const double* __restrict__ a, const double* __restrict__ c,
+                                                  double* __restrict__ partial, long long len, ScalarTail tl) {
+  const long long rb = (long long)blockIdx.y * len;
+  double* pr = partial + (long long)blockIdx.y * gridDim.x;
+  dot_body(a + rb, c + rb, pr + blockIdx.x, len, blockIdx.x, gridDim.x);
+  scalar_tail(tl, blockIdx.y, pr, gridDim.x, gridDim.x);
+}
+
 __device__ __forceinline__ void vupdate_body(const double* __restrict__ T, const double* __restrict__ v,
                                              double* __restrict__ vprev, const MinresScalars& S, long long len,
                                              int bx, int nbx) {
@@ -70,20 +81,36 @@ __global__ void __launch_bounds__(VNT) k_vupdate(const double* __restrict__ T, c
   vupdate_body(T + rb, v + rb, vprev + rb, sc[blockIdx.y], len, blockIdx.x, gridDim.x);
 }
 
+__device__ __forceinline__ void wxupdate_run(const double* __restrict__ z, double* __restrict__ wprev,
+                                             const double* __restrict__ w, double* __restrict__ x,
+                                             const MinresScalars* __restrict__ sc, long long len) {
+  const MinresScalars& S = sc[blockIdx.y];
+  if (!S.done) {
+    const long long rb = (long long)blockIdx.y * len;
+    const double c0 = S.cw[0], c1 = S.cw[1], c2 = S.cw[2], c3 = S.cw[3];
+#pragma unroll 4
+    for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT) {
+      const long long k = rb + i;
+      const double wn = fma(c0, z[k], fma(c1, wprev[k], c2 * w[k]));
+      wprev[k] = wn;
+      x[k] = fma(c3, wn, x[k]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(VNT) k_wxupdate(const double* __restrict__ z, double* __restrict__ wprev,
                                                   const double* __restrict__ w, double* __restrict__ x,
                                                   const MinresScalars* __restrict__ sc, long long len) {
-  const MinresScalars& S = sc[blockIdx.y];
-  if (S.done) return;
-  const long long rb = (long long)blockIdx.y * len;
-  const double c0 = S.cw[0], c1 = S.cw[1], c2 = S.cw[2], c3 = S.cw[3];
-#pragma unroll 4
-  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT) {
-    const long long k = rb + i;
-    const double wn = fma(c0, z[k], fma(c1, wprev[k], c2 * w[k]));
-    wprev[k] = wn;
-    x[k] = fma(c3, wn, x[k]);
-  }
+  wxupdate_run(z, wprev, w, x, sc, len);
+}
+
+// with step 4 (the recurrence-estimate stop test, no partial sums) in the tail
+__global__ void __launch_bounds__(VNT, 8) k_wxupdate_tail(const double* __restrict__ z, double* __restrict__ wprev,
+                                                       const double* __restrict__ w, double* __restrict__ x,
+                                                       const MinresScalars* __restrict__ sc, long long len,
+                                                       ScalarTail tl) {
+  wxupdate_run(z, wprev, w, x, sc, len);
+  scalar_tail(tl, blockIdx.y, nullptr, 0, gridDim.x);
 }
 
 __global__ void k_set_params(double* prm, double rtol, int maxit) {
@@ -115,126 +142,11 @@ __global__ void __launch_bounds__(VNT) k_axpy(double a, const double* __restrict
     y[i] = fma(a, x[i], y[i]);
 }
 
-// deterministic sum of nb partials of right-hand side r by one warp
-// (eight independent running sums per lane keep eight loads in flight; fixed order)
-__device__ __forceinline__ double sum_partials(const double* p, int nb) {
-  double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int i = threadIdx.x;
-  for (; i + 7 * 32 < nb; i += 8 * 32) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) t[u] += p[i + 32 * u];
-  }
-  for (; i < nb; i += 32) t[0] += p[i];
-  return warp_sum(((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7])));
-}
-
-// One warp: the scalar step of one right-hand side from its partial sums p1 (and, at
-// step 0, p2 and p3), in a fixed order.
-__device__ __forceinline__ void scalars_body(int step, MinresScalars& S, const double* __restrict__ p1,
-                                             int nb1, const double* __restrict__ p2, int nb2,
-                                             const double* __restrict__ p3, int nb3, double rtol, int maxit,
-                                             const double* __restrict__ prm) {
-  const double s1 = sum_partials(p1, nb1);
-  double s2 = 0.0, s3 = 0.0;
-  if (step == 0) {
-    s2 = sum_partials(p2, nb2);
-    s3 = sum_partials(p3, nb3);
-  }
-  if (threadIdx.x != 0) return;
-  if (step == 0) {
-    // s1 = <z1, v1>, s2 = <b, b>, s3 = <v1, v1>; rtol and maxit from prm when given
-    S.rtol = prm ? prm[0] : rtol;
-    S.maxit = prm ? (int)prm[1] : maxit;
-    S.iters = 0;
-    S.status = AAO_OK;
-    S.done = 0;
-    S.bnorm2 = (s2 > 0.0) ? s2 : 1.0;
-    S.relres_true = sqrt(s3 / S.bnorm2);
-    S.relres_est = 1.0;
-    S.gam_prev = 1.0;
-    S.c = S.c_prev = 1.0;
-    S.s = S.s_prev = 0.0;
-    S.delta = 0.0;
-    for (int i = 0; i < 3; ++i) S.cv[i] = 0.0;
-    for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
-    if (s1 < 0.0) { S.status = AAO_EBREAKDOWN; S.done = 1; }
-    if (s1 == 0.0 || S.relres_true <= S.rtol) S.done = 1;
-    S.gam = S.done ? 0.0 : sqrt(s1);
-    S.gam1 = S.gam;
-    S.eta = S.gam;
-    return;
-  }
-  if (S.done) {
-    for (int i = 0; i < 3; ++i) S.cv[i] = 0.0;
-    for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
-    return;
-  }
-  if (step == 1) {
-    const double g = S.gam;
-    S.delta = s1 / (g * g);
-    S.cv[0] = 1.0 / g;
-    S.cv[1] = -S.delta / g;
-    S.cv[2] = -g / S.gam_prev;
-  } else if (step == 2) {
-    if (s1 < 0.0) {
-      S.status = AAO_EBREAKDOWN;
-      S.done = 1;
-      for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
-      return;
-    }
-    const double gn = sqrt(s1);
-    const double g = S.gam, dl = S.delta;
-    const double a0 = S.c * dl - S.c_prev * S.s * g;
-    const double a1 = sqrt(a0 * a0 + gn * gn);
-    const double a2 = S.s * dl + S.c_prev * S.c * g;
-    const double a3 = S.s_prev * g;
-    if (a1 == 0.0) {
-      S.status = AAO_EBREAKDOWN;
-      S.done = 1;
-      for (int i = 0; i < 4; ++i) S.cw[i] = 0.0;
-      return;
-    }
-    const double cn = a0 / a1, sn = gn / a1;
-    S.cw[0] = 1.0 / (g * a1);
-    S.cw[1] = -a3 / a1;
-    S.cw[2] = -a2 / a1;
-    S.cw[3] = cn * S.eta;
-    S.eta = -sn * S.eta;
-    S.gam_prev = g;
-    S.gam = gn;
-    S.c_prev = S.c;
-    S.c = cn;
-    S.s_prev = S.s;
-    S.s = sn;
-    S.iters += 1;
-    S.relres_est = fabs(S.eta) / S.gam1;
-  } else if (step == 4) {
-    // stop on the recurrence estimate (inner solves of the refinement loop, whose
-    // outer loop recomputes the true residual)
-    if (S.relres_est <= S.rtol) {
-      S.done = 1;
-      S.status = AAO_OK;
-    } else if (S.iters >= S.maxit || S.gam == 0.0) {
-      S.done = 1;
-      S.status = AAO_ENOTCONV;
-    }
-  } else if (step == 3) {
-    S.relres_true = sqrt(s1 / S.bnorm2);
-    if (S.relres_true <= S.rtol) {
-      S.done = 1;
-      S.status = AAO_OK;
-    } else if (S.iters >= S.maxit || S.gam == 0.0) {
-      S.done = 1;
-      S.status = AAO_ENOTCONV;
-    }
-  }
-}
-
 __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict__ p1, int nb1,
                           const double* __restrict__ p2, int nb2, const double* __restrict__ p3,
                           int nb3, double rtol, int maxit, const double* __restrict__ prm) {
   const int r = blockIdx.x;
-  scalars_body(step, sc[r], p1 + (long long)r * nb1, nb1, p2 + (long long)r * nb2, nb2,
+  scalars_body<false>(step, sc[r], p1 + (long long)r * nb1, nb1, p2 + (long long)r * nb2, nb2,
                p3 + (long long)r * nb3, nb3, rtol, maxit, prm);
 }
 
@@ -242,24 +154,16 @@ __global__ void k_scalars(int step, MinresScalars* sc, const double* __restrict_
 __global__ void k_relres(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2,
                          double* __restrict__ relres) {
   const int r = blockIdx.x;
-  const double s1 = sum_partials(p1 + (long long)r * nb1, nb1);
-  const double s2 = sum_partials(p2 + (long long)r * nb2, nb2);
+  const double s1 = sum_partials<false>(p1 + (long long)r * nb1, nb1);
+  const double s2 = sum_partials<false>(p2 + (long long)r * nb2, nb2);
   if (threadIdx.x == 0) relres[r] = (s2 > 0.0) ? sqrt(s1 / s2) : sqrt(s1);
 }
 
-// Device-side loop control for the graph-captured solve: counts the trip and sets
-// the WHILE condition to "some right-hand side still iterating and trips < limit"
-// (the limit bounds the loop whatever the scalar state holds).
+// Device-side loop control for the graph-captured solve (loop_cond_body).
 __global__ void k_loop_cond(cudaGraphConditionalHandle hw, const MinresScalars* __restrict__ sc, int nrhs,
                             int* trips, int trip_limit, int count, const double* __restrict__ prm) {
   if (threadIdx.x != 0) return;
-  if (prm) trip_limit = (int)prm[1] / 2 + 2;  // two iterations per trip
-  const int t = *trips + count;
-  *trips = t;
-  bool any = false;
-  for (int r = 0; r < nrhs; ++r)
-    if (!sc[r].done) any = true;
-  cudaGraphSetConditional(hw, (any && t < trip_limit) ? 1u : 0u);
+  loop_cond_body<false>(hw, sc, nrhs, trips, trip_limit, count, prm);
 }
 
 // ---- grouped launches (serving): see GroupRound ----
@@ -286,7 +190,7 @@ __global__ void k_g_scalars(int step, const GroupRound* __restrict__ g) {
   const int r = blockIdx.x;
   const GroupProblem& P = g->p[r];
   const int nb = step == 1 ? g->yt[r + 1] - g->yt[r] : step == 2 ? P.nb_dot : g->wx[r + 1] - g->wx[r];
-  scalars_body(step, *P.sc, P.partial, nb, nullptr, 0, nullptr, 0, 0.0, 0, nullptr);
+  scalars_body<false>(step, *P.sc, P.partial, nb, nullptr, 0, nullptr, 0, 0.0, 0, nullptr);
   if (step == 3 && threadIdx.x == 0) g->flags[r] = P.sc->done;
 }
 
@@ -327,9 +231,11 @@ cudaError_t launch_group_scalars(int step, const GroupRound* d_round, int count,
 }
 
 cudaError_t launch_dot(const Plan& P, const double* a, const double* c, double* partial, int nrhs,
-                       cudaStream_t s, uint64_t* nl) {
+                       cudaStream_t s, uint64_t* nl, const ScalarTail* tail) {
   if (nl) ++*nl;
-  k_dot<<<dim3(dot_blocks_per_rhs(P), nrhs), VNT, 0, s>>>(a, c, partial, (long long)P.n * P.m);
+  const dim3 g(dot_blocks_per_rhs(P), nrhs);
+  if (tail) k_dot_tail<<<g, VNT, 0, s>>>(a, c, partial, (long long)P.n * P.m, *tail);
+  else k_dot<<<g, VNT, 0, s>>>(a, c, partial, (long long)P.n * P.m);
   return cudaGetLastError();
 }
 
@@ -342,9 +248,10 @@ cudaError_t launch_vupdate(const Plan& P, const double* T, const double* v, doub
 
 cudaError_t launch_wxupdate(const Plan& P, const double* z, double* wprev_out, const double* w,
                             double* x, const MinresScalars* sc, int nrhs, cudaStream_t s,
-                            uint64_t* nl) {
+                            uint64_t* nl, const ScalarTail* tail) {
   if (nl) ++*nl;
-  k_wxupdate<<<vgrid(P, nrhs), VNT, 0, s>>>(z, wprev_out, w, x, sc, (long long)P.n * P.m);
+  if (tail) k_wxupdate_tail<<<vgrid(P, nrhs), VNT, 0, s>>>(z, wprev_out, w, x, sc, (long long)P.n * P.m, *tail);
+  else k_wxupdate<<<vgrid(P, nrhs), VNT, 0, s>>>(z, wprev_out, w, x, sc, (long long)P.n * P.m);
   return cudaGetLastError();
 }
 

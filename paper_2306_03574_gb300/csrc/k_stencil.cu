@@ -10,6 +10,7 @@
 // reductions: sum (YTv)*w  (the MINRES delta), or sum (w - YTv)^2 (the true
 // residual, with w = b).
 #include "aao_internal.cuh"
+#include "minres_scalars.cuh"
 
 namespace aao {
 
@@ -17,6 +18,14 @@ namespace {
 
 constexpr int YT_NT = 256;
 constexpr int YT_CH = 32;
+// Resident blocks per SM of the stencil kernels with a fused scalar step in their tail
+// (minres_scalars.cuh): the register budgets of the same kernels without it, so that the
+// step's registers (spilled if need be; it runs once per right-hand side) do not lower
+// the main loop's occupancy.
+constexpr int yt_min_blocks(int D, int MODE) { return MODE == 2 && D < 3 ? 6 : 8; }
+constexpr int ytv_min_blocks(int D, int MODE) {
+  return D == 1 ? (MODE == 2 ? 6 : 8) : D == 2 ? (MODE == 2 ? 4 : 6) : 5;
+}
 
 struct YtArgs {
   int N, n, m;
@@ -51,9 +60,9 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(YT_NT) k_yt(const double* __restrict__ x, double* __restrict__ y,
-                                              const double* __restrict__ w,
-                                              double* __restrict__ partial, YtArgs a) {
+__device__ __forceinline__ void yt_run(const double* __restrict__ x, double* __restrict__ y,
+                                       const double* __restrict__ w, double* __restrict__ partial,
+                                       const YtArgs& a) {
   const int s = blockIdx.x * YT_NT + threadIdx.x;
   const int n = a.n, m = a.m, N = a.N;
   const int i0 = blockIdx.y * YT_CH;
@@ -86,11 +95,27 @@ __global__ void __launch_bounds__(YT_NT) k_yt(const double* __restrict__ x, doub
   }
   if (MODE != 0) {
     const double t = block_sum(acc);
-    if (threadIdx.x == 0) {
-      const long long nb = (long long)gridDim.x * gridDim.y;
-      partial[blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
-    }
+    const int nb = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) partial[(long long)blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
+}
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(YT_NT) k_yt(const double* __restrict__ x, double* __restrict__ y,
+                                              const double* __restrict__ w, double* __restrict__ partial,
+                                              YtArgs a) {
+  yt_run<D, MODE>(x, y, w, partial, a);
+}
+
+// The same with a MINRES scalar step on the partials in the tail (modes 1, 2).  A kernel
+// of its own so that the step's registers do not change the budget of k_yt.
+template <int D, int MODE>
+__global__ void __launch_bounds__(YT_NT, yt_min_blocks(D, MODE))
+    k_yt_tail(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ w,
+              double* __restrict__ partial, YtArgs a, ScalarTail tl) {
+  yt_run<D, MODE>(x, y, w, partial, a);
+  const int nb = gridDim.x * gridDim.y;
+  scalar_tail(tl, blockIdx.z, partial + (long long)blockIdx.z * nb, nb, nb);
 }
 
 // The same operator in the DST basis: with U = S (x)..(x) S orthogonal and symmetric,
@@ -136,15 +161,33 @@ __device__ __forceinline__ void ythat_body(const double* __restrict__ x, double*
 }
 
 template <int MODE>
+__device__ __forceinline__ void ythat_run(const double* __restrict__ x, double* __restrict__ y,
+                                          const double* __restrict__ w, double* __restrict__ partial,
+                                          const double* __restrict__ lam, const YtArgs& a) {
+  const long long rb = (long long)blockIdx.z * a.n * a.m;
+  const int nb = gridDim.x * gridDim.y;
+  double* part = MODE != 0 ? partial + (long long)blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x
+                           : nullptr;
+  ythat_body<MODE>(x + rb, y ? y + rb : nullptr, w ? w + rb : nullptr, part, lam, a.n, a.m, blockIdx.x,
+                   blockIdx.y);
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(YT_NT) k_ythat(const double* __restrict__ x, double* __restrict__ y,
                                                  const double* __restrict__ w,
                                                  double* __restrict__ partial,
                                                  const double* __restrict__ lam, YtArgs a) {
-  const long long rb = (long long)blockIdx.z * a.n * a.m;
-  const long long nb = (long long)gridDim.x * gridDim.y;
-  double* part = MODE != 0 ? partial + blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x : nullptr;
-  ythat_body<MODE>(x + rb, y ? y + rb : nullptr, w ? w + rb : nullptr, part, lam, a.n, a.m, blockIdx.x,
-                   blockIdx.y);
+  ythat_run<MODE>(x, y, w, partial, lam, a);
+}
+
+// with a MINRES scalar step on the partials in the tail (modes 1..3)
+template <int MODE>
+__global__ void __launch_bounds__(YT_NT, 8)
+    k_ythat_tail(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ w,
+                 double* __restrict__ partial, const double* __restrict__ lam, YtArgs a, ScalarTail tl) {
+  ythat_run<MODE>(x, y, w, partial, lam, a);
+  const int nb = gridDim.x * gridDim.y;
+  scalar_tail(tl, blockIdx.z, partial + (long long)blockIdx.z * nb, nb, nb);
 }
 
 // One MINRES step's direction and iterate update fused with the true residual, in the
@@ -213,8 +256,20 @@ __global__ void __launch_bounds__(WXR_NT) k_wx_res(const double* __restrict__ z,
                                                    const MinresScalars* __restrict__ sc,
                                                    double* __restrict__ partial, int n, int m) {
   const long long rb = (long long)blockIdx.y * n * m;
-  wx_res_body(z + rb, wprev + rb, w + rb, x + rb, b + rb, lam, sc[blockIdx.y],
-              partial + (long long)blockIdx.y * gridDim.x + blockIdx.x, n, m, blockIdx.x);
+  double* pr = partial + (long long)blockIdx.y * gridDim.x;
+  wx_res_body(z + rb, wprev + rb, w + rb, x + rb, b + rb, lam, sc[blockIdx.y], pr + blockIdx.x, n, m, blockIdx.x);
+}
+
+// with the stop test (MINRES scalar step 3) in the tail
+__global__ void __launch_bounds__(WXR_NT, 12) k_wx_res_tail(const double* __restrict__ z, double* __restrict__ wprev,
+                                                   const double* __restrict__ w, double* __restrict__ x,
+                                                   const double* __restrict__ b, const double* __restrict__ lam,
+                                                   const MinresScalars* __restrict__ sc,
+                                                   double* __restrict__ partial, int n, int m, ScalarTail tl) {
+  const long long rb = (long long)blockIdx.y * n * m;
+  double* pr = partial + (long long)blockIdx.y * gridDim.x;
+  wx_res_body(z + rb, wprev + rb, w + rb, x + rb, b + rb, lam, sc[blockIdx.y], pr + blockIdx.x, n, m, blockIdx.x);
+  scalar_tail(tl, blockIdx.y, pr, gridDim.x, gridDim.x);
 }
 
 // ---- grouped launches (serving): see GroupRound ----
@@ -319,9 +374,9 @@ __device__ __forceinline__ double apply_La(const double* __restrict__ v, int s, 
 }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(YT_NT) k_yt_var(const double* __restrict__ x, double* __restrict__ y,
-                                                  const double* __restrict__ w,
-                                                  double* __restrict__ partial, VarArgs a) {
+__device__ __forceinline__ void yt_var_run(const double* __restrict__ x, double* __restrict__ y,
+                                           const double* __restrict__ w, double* __restrict__ partial,
+                                           const VarArgs& a) {
   const int s = blockIdx.x * YT_NT + threadIdx.x;
   const int n = a.n, m = a.m, N = a.N;
   const int i0 = blockIdx.y * YT_CH;
@@ -355,11 +410,26 @@ __global__ void __launch_bounds__(YT_NT) k_yt_var(const double* __restrict__ x, 
   }
   if (MODE != 0) {
     const double t = block_sum(acc);
-    if (threadIdx.x == 0) {
-      const long long nb = (long long)gridDim.x * gridDim.y;
-      partial[blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
-    }
+    const int nb = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) partial[(long long)blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
+}
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(YT_NT) k_yt_var(const double* __restrict__ x, double* __restrict__ y,
+                                                  const double* __restrict__ w, double* __restrict__ partial,
+                                                  VarArgs a) {
+  yt_var_run<D, MODE>(x, y, w, partial, a);
+}
+
+// with a MINRES scalar step on the partials in the tail (modes 1, 2)
+template <int D, int MODE>
+__global__ void __launch_bounds__(YT_NT, ytv_min_blocks(D, MODE))
+    k_yt_var_tail(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ w,
+                  double* __restrict__ partial, VarArgs a, ScalarTail tl) {
+  yt_var_run<D, MODE>(x, y, w, partial, a);
+  const int nb = gridDim.x * gridDim.y;
+  scalar_tail(tl, blockIdx.z, partial + (long long)blockIdx.z * nb, nb, nb);
 }
 
 template <int D>
@@ -448,11 +518,13 @@ cudaError_t launch_group_wx_res(const GroupRound* d_round, int total_blocks, cud
 
 cudaError_t launch_wx_res(const Plan& P, const double* lam, const double* z, double* wprev_out,
                           const double* w, double* x, const double* b, const MinresScalars* sc,
-                          double* partial, int nrhs, cudaStream_t s, uint64_t* nl, int* nb) {
+                          double* partial, int nrhs, cudaStream_t s, uint64_t* nl, int* nb,
+                          const ScalarTail* tail) {
   if (nl) ++*nl;
   const dim3 g(wxres_blocks_per_rhs(P), nrhs);
   if (nb) *nb = (int)g.x;
-  k_wx_res<<<g, WXR_NT, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m);
+  if (tail) k_wx_res_tail<<<g, WXR_NT, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m, *tail);
+  else k_wx_res<<<g, WXR_NT, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m);
   return cudaGetLastError();
 }
 
@@ -462,34 +534,42 @@ int yt_blocks_per_rhs(const Plan& P) {
 
 template <int D>
 static void yt_dispatch(int mode, dim3 g, cudaStream_t s, const double* x, double* y,
-                        const double* w, double* partial, const YtArgs& a) {
+                        const double* w, double* partial, const YtArgs& a, const ScalarTail& tl) {
   if (mode == 0) k_yt<D, 0><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
+  else if (tl.sc && mode == 1) k_yt_tail<D, 1><<<g, YT_NT, 0, s>>>(x, y, w, partial, a, tl);
+  else if (tl.sc) k_yt_tail<D, 2><<<g, YT_NT, 0, s>>>(x, y, w, partial, a, tl);
   else if (mode == 1) k_yt<D, 1><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
   else k_yt<D, 2><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
 }
 
 cudaError_t launch_yt(const Plan& P, const double* x, double* y, const double* w, double* partial,
-                      int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb) {
+                      int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb, const ScalarTail* tail) {
   if (nl) ++*nl;
   const YtArgs a = make_args(P);
   dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
   if (nb) *nb = (int)(g.x * g.y);
+  const ScalarTail tl = tail ? *tail : ScalarTail{};
   switch (P.d) {
-    case 1: yt_dispatch<1>(mode, g, s, x, y, w, partial, a); break;
-    case 2: yt_dispatch<2>(mode, g, s, x, y, w, partial, a); break;
-    case 3: yt_dispatch<3>(mode, g, s, x, y, w, partial, a); break;
+    case 1: yt_dispatch<1>(mode, g, s, x, y, w, partial, a, tl); break;
+    case 2: yt_dispatch<2>(mode, g, s, x, y, w, partial, a, tl); break;
+    case 3: yt_dispatch<3>(mode, g, s, x, y, w, partial, a, tl); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, double* y, const double* w,
-                        double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb) {
+                        double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb,
+                        const ScalarTail* tail) {
   if (nl) ++*nl;
   const YtArgs a = make_args(P);
   dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
   if (nb) *nb = (int)(g.x * g.y);
+  const ScalarTail tl = tail ? *tail : ScalarTail{};
   if (mode == 0) k_ythat<0><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
+  else if (tl.sc && mode == 1) k_ythat_tail<1><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a, tl);
+  else if (tl.sc && mode == 2) k_ythat_tail<2><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a, tl);
+  else if (tl.sc) k_ythat_tail<3><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a, tl);
   else if (mode == 1) k_ythat<1><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
   else if (mode == 2) k_ythat<2><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
   else k_ythat<3><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
@@ -509,22 +589,26 @@ static VarArgs make_var(const Plan& P, const double* face) {
 
 template <int D>
 static void ytv_dispatch(int mode, dim3 g, cudaStream_t s, const double* x, double* y,
-                         const double* w, double* partial, const VarArgs& a) {
+                         const double* w, double* partial, const VarArgs& a, const ScalarTail& tl) {
   if (mode == 0) k_yt_var<D, 0><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
+  else if (tl.sc && mode == 1) k_yt_var_tail<D, 1><<<g, YT_NT, 0, s>>>(x, y, w, partial, a, tl);
+  else if (tl.sc) k_yt_var_tail<D, 2><<<g, YT_NT, 0, s>>>(x, y, w, partial, a, tl);
   else if (mode == 1) k_yt_var<D, 1><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
   else k_yt_var<D, 2><<<g, YT_NT, 0, s>>>(x, y, w, partial, a);
 }
 
 cudaError_t launch_yt_var(const Plan& P, const double* face, const double* x, double* y, const double* w,
-                          double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb) {
+                          double* partial, int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb,
+                          const ScalarTail* tail) {
   if (nl) ++*nl;
   const VarArgs a = make_var(P, face);
   dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
   if (nb) *nb = (int)(g.x * g.y);
+  const ScalarTail tl = tail ? *tail : ScalarTail{};
   switch (P.d) {
-    case 1: ytv_dispatch<1>(mode, g, s, x, y, w, partial, a); break;
-    case 2: ytv_dispatch<2>(mode, g, s, x, y, w, partial, a); break;
-    case 3: ytv_dispatch<3>(mode, g, s, x, y, w, partial, a); break;
+    case 1: ytv_dispatch<1>(mode, g, s, x, y, w, partial, a, tl); break;
+    case 2: ytv_dispatch<2>(mode, g, s, x, y, w, partial, a, tl); break;
+    case 3: ytv_dispatch<3>(mode, g, s, x, y, w, partial, a, tl); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -337,6 +337,9 @@ static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrh
   const int v = std::is_same<R, double>::value  ? P.time_variant64
                 : std::is_same<R, float>::value ? P.time_variant32
                                                 : P.time_variant_ff;
+  // small-problem tile: one warp, small_pairs(L) mode pairs, radix-4 plan, sequence-major
+  if (v == TIME_VARIANT_SMALL)
+    return time_launch_cfg<R, TIO, L, small_pairs(L), SMALL_NT, 0, 0>(P, in, out, nrhs, s);
   if constexpr (std::is_same<R, float>::value && std::is_same<TIO, float>::value) {
     // FP32 vectors: the variants of the FP64-vector kernel above 7 map to the classic
     // layout of their tile (full: 5, half: 7)

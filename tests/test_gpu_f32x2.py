@@ -67,7 +67,9 @@ def test_f32x2_time_variants(d, N, nt, monkeypatch):
     m = N ** d
     x = W.random_field((nt, m), seed=2400 + nt)
     ref = OF.time_part_modes(d, N, nt, tau, alpha, x, np.arange(m))
-    for v in range(14):  # 8..11: interleaved layout without the staged table slice; 12, 13 batched loads
+    # 8..11: interleaved layout without the staged table slice; 12, 13 batched loads;
+    # 30 the one-warp small-problem tile
+    for v in list(range(14)) + [30]:
         monkeypatch.setenv("AAO_TIME_VARIANT", f"{v},{v},{v}")
         with aao.Solver(d, N, nt, tau, alpha, precision=aao.AAO_PREC_F32X2) as s:
             xt = cu(x)
@@ -141,7 +143,7 @@ def test_f32x2_dst_parity(d, N, monkeypatch):
     nt = 64
     x = W.random_field((nt, N ** d), seed=2500 + N + d)
     ref = OF.apply_space(x, OF.dst_matrix(N), d, N)
-    for dv in range(4):
+    for dv in range(5):  # 4: the one-warp small-problem tile
         monkeypatch.setenv("AAO_DST_VARIANT", str(dv))
         with aao.Solver(d, N, nt, 1.0 / nt, 0.1, precision=aao.AAO_PREC_F32X2) as s:
             xt = cu(x)

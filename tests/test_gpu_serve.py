@@ -1,6 +1,8 @@
 """Serving: requests of mixed sizes, wave speeds, alpha and tolerances admitted onto
 the GPU concurrently under an HBM budget; each result is bit-for-bit the result of
 the same solve run alone; budget eviction, an oversize request, bounded waits."""
+import contextlib
+import os
 import time
 
 import numpy as np
@@ -37,8 +39,25 @@ def _requests(k=24, seed=77):
     return out
 
 
+@contextlib.contextmanager
+def _standard_tiles():
+    """Served handles run their time pipelines in grouped launches with the standard
+    tiles (time variants 3 / 24 / 12), also where a handle alone would take the
+    small-problem tile: the solo reference solves are pinned to the same variants so
+    that their bits can be compared (read when the handle is created)."""
+    old = os.environ.get("AAO_TIME_VARIANT")
+    os.environ["AAO_TIME_VARIANT"] = "3,24,12"
+    try:
+        yield
+    finally:
+        if old is None:
+            del os.environ["AAO_TIME_VARIANT"]
+        else:
+            os.environ["AAO_TIME_VARIANT"] = old
+
+
 def _solo(p, rtol):
-    with aao.Solver(p.d, p.N, p.nt, p.tau, p.alpha, c2=p.c2, graph=True) as s:
+    with _standard_tiles(), aao.Solver(p.d, p.N, p.nt, p.tau, p.alpha, c2=p.c2, graph=True) as s:
         b = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
         s.build_rhs(cu(p.f), cu(p.psi0), cu(p.psi1), b)
         x = torch.empty_like(b)
@@ -158,7 +177,8 @@ def test_served_precisions_equal_solo_solves():
     finally:
         aao.aao_serve_destroy(srv)
     for (prec, _), (r, p, f, p0, p1, x), res in zip(tickets, reqs, results):
-        with aao.Solver(p.d, p.N, p.nt, p.tau, p.alpha, c2=p.c2, precision=prec, graph=True) as s:
+        with _standard_tiles(), aao.Solver(p.d, p.N, p.nt, p.tau, p.alpha, c2=p.c2, precision=prec,
+                                           graph=True) as s:
             b = torch.empty((p.nt, p.m), dtype=torch.float64, device="cuda")
             s.build_rhs(f, p0, p1, b)
             xs = torch.empty_like(b)

@@ -1,5 +1,6 @@
-"""Every kernel variant computes the same values: the eight time-pipeline variants
-(FFT stage plan x tile x shared-memory layout) and the two DST stage plans, each
+"""Every kernel variant computes the same values: the time-pipeline variants (FFT stage
+plan x tile x shared-memory layout x load staging, and the small-problem tile) and the
+DST variants (stage plan x batched loads, and the small-problem tile), each
 against the oracle in FP64 and in FP32, at every supported time length with ragged
 mode tails.  The variants only change speed, so each must pass the same gates."""
 import os
@@ -58,10 +59,12 @@ def test_time_variants(d, N, nt, monkeypatch):
     outs = []
     # FP32 on FP64 vectors: 8..15 bulk-staged tile, 16, 17 integer conversions, 18..21
     # loads batched ahead of their conversion, 22, 23 spectral table computed on the fly,
-    # 24..29 batched loads with integer conversions of the stores, the loads or both
-    for v in range(30):
-        monkeypatch.setenv("AAO_TIME_VARIANT", f"{v & 7},{v}")
-        for prec in (aao.AAO_PREC_FP64, aao.AAO_PREC_FP32_IR) if v < 8 else (aao.AAO_PREC_FP32_IR,):
+    # 24..29 batched loads with integer conversions of the stores, the loads or both;
+    # 30 the one-warp small-problem tile (every precision)
+    for v in list(range(30)) + [30]:
+        monkeypatch.setenv("AAO_TIME_VARIANT", f"{v if v == 30 else v & 7},{v}")
+        both = v < 8 or v == 30
+        for prec in (aao.AAO_PREC_FP64, aao.AAO_PREC_FP32_IR) if both else (aao.AAO_PREC_FP32_IR,):
             with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=prec) as s:
                 xt = cu(x)
                 yt = torch.empty_like(xt)
@@ -124,8 +127,8 @@ def test_dst_and_prec_variants(d, N, nt, monkeypatch):
     ref_dst = OF.apply_space(x, S, d, N)
     ref_prec = OF.ABACPreconditioner(d, N, nt, 1.0 / nt, ALPHA).apply(x)
     tol32 = gates.fp32("prec", d, N, nt, ALPHA)
-    for dv in range(4):
-        for tv in (1, 5):
+    for dv in range(5):  # 4: the one-warp small-problem tile
+        for tv in (1, 5, 30):
             monkeypatch.setenv("AAO_DST_VARIANT", str(dv))
             monkeypatch.setenv("AAO_TIME_VARIANT", f"{tv},{tv}")
             with aao.Solver(d, N, nt, 1.0 / nt, ALPHA) as s:
