@@ -126,8 +126,12 @@ typedef struct aao_handle aao_handle;
  * Tuning overrides (environment, read here; for measurements and tests):
  *   AAO_TIME_VARIANT="v64[,v32[,vff]]" sets the time-kernel variant per precision
  *   (the numbering of aao_autotune; a missing entry repeats the previous one), and
- *   AAO_DST_VARIANT="0..3" the DST variant (bit 0: radix-16-first stage plan, bit 1:
- *   batched loads), and AAO_FUSED_SCALARS=1 runs the MINRES scalar steps in the tails
+ *   AAO_DST_VARIANT="0..4" the DST variant (bit 0: radix-16-first stage plan, bit 1:
+ *   batched loads; 4: the one-warp small-problem tile), AAO_SMALL_TILES=0 keeps the
+ *   standard tiles for a small problem (by default a problem whose standard tiles
+ *   would occupy fewer than a quarter of the SMs gets the one-warp time (variant 30)
+ *   and DST tiles, operator runs of 4 time levels and the small w/x update shape;
+ *   served handles always keep the standard tiles), and AAO_FUSED_SCALARS=1 runs the MINRES scalar steps in the tails
  *   of the kernels that produce their partial sums (five launches per iteration instead
  *   of eight, and no separate loop-condition launch in a graph trip).  Every variant
  *   computes the same values (bit for bit, for the fused scalar steps).

@@ -949,17 +949,41 @@ aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double 
   return AAO_OK;
 }
 
+// Small problems: where the standard tiles give fewer CTAs than a quarter of the 152
+// SMs, kernels with smaller tiles spread the work wider (1D 63 x 64: the time pipeline
+// and the DST run on 16 CTAs instead of 1, the operator on 16 instead of 2): the
+// one-warp time and DST tiles (when even the half tile -- 2048/n mode pairs, 2048/(N+1)
+// line pairs -- is too coarse), short stencil runs, the small w/x update shape.
+static void choose_small_tiles(Plan& P) {
+  constexpr long long few = 152 / 4;
+  const int nt = P.n, M = P.M;
+  if ((P.npairs + 2048 / nt - 1) / (2048 / nt) < few)
+    P.time_variant64 = P.time_variant32 = P.time_variant_ff = TIME_VARIANT_SMALL;
+  const long long lines = (long long)nt * P.m / P.N, ns = 2048 / M;
+  if ((lines + 2 * ns - 1) / (2 * ns) < few) P.dst_variant = DST_VARIANT_SMALL;
+  if ((long long)((P.m + YT_THREADS - 1) / YT_THREADS) * ((nt + YT_CH_STD - 1) / YT_CH_STD) < few)
+    P.yt_ch = YT_CH_SMALL;
+  if ((P.m + 31) / 32 < few) P.wx_small = 1;
+}
+
+// Back to the standard tiles (the variants of a handle created without small tiles).
+static void use_standard_tiles(Plan& P, int precision) {
+  const Plan standard;
+  if (P.time_variant64 == TIME_VARIANT_SMALL) P.time_variant64 = standard.time_variant64;
+  if (P.time_variant32 == TIME_VARIANT_SMALL) P.time_variant32 = standard.time_variant32;
+  if (P.time_variant_ff == TIME_VARIANT_SMALL) P.time_variant_ff = standard.time_variant_ff;
+  if (P.dst_variant == DST_VARIANT_SMALL) P.dst_variant = precision == AAO_PREC_FP64 ? 1 : 3;
+  P.yt_ch = standard.yt_ch;
+  P.wx_small = standard.wx_small;
+}
+
 // ---- grouped serving (aao_serve.cu): one problem per handle, iterations run by grouped launches ----
 aao_status aaoi_serving_prepare(aao_handle* h) {
   if (!h) return fail(AAO_EINVAL, "null handle");
   if (h->pin) return AAO_OK;
-  // served problems run their time pipelines in grouped launches, which take the
-  // standard tiles: a small problem keeps them too (its CTAs share the grouped grid)
-  Plan& Pm = h->P;
-  const Plan standard;
-  if (Pm.time_variant64 == TIME_VARIANT_SMALL) Pm.time_variant64 = standard.time_variant64;
-  if (Pm.time_variant32 == TIME_VARIANT_SMALL) Pm.time_variant32 = standard.time_variant32;
-  if (Pm.time_variant_ff == TIME_VARIANT_SMALL) Pm.time_variant_ff = standard.time_variant_ff;
+  // served problems run their iterations in grouped launches, which take the standard
+  // tiles: a small problem keeps them too (its CTAs share the grouped grid)
+  use_standard_tiles(h->P, h->precision);
   const Plan& P = h->P;
   const size_t nt = (size_t)P.n;
   const size_t bytes = 2 * nt * sizeof(double2) + 2 * nt * sizeof(double) + (size_t)P.m * sizeof(double) +
@@ -1179,15 +1203,9 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   // DST default: the FP64 DST is bound by the FP64 pipe; the double-float and FP32 DSTs
   // (the handle's DSTs in the other modes) gain from batched loads (measured on GB300)
   P.dst_variant = o.precision == AAO_PREC_FP64 ? 1 : 3;
-  // Small problems: when even the half tile (2048/n mode pairs, 2048/(N+1) line pairs)
-  // gives fewer CTAs than a quarter of the 152 SMs, the one-warp small tiles spread the
-  // work wider (C1, 1D 63 x 64: 1 CTA -> 16).
-  if ((P.npairs + 2048 / nt - 1) / (2048 / nt) < 38) {
-    P.time_variant64 = P.time_variant32 = P.time_variant_ff = TIME_VARIANT_SMALL;
-  }
   {
-    const long long lines = (long long)nt * P.m / P.N, ns = 2048 / M;
-    if ((lines + 2 * ns - 1) / (2 * ns) < 38) P.dst_variant = DST_VARIANT_SMALL;
+    const char* st_env = getenv("AAO_SMALL_TILES");
+    if (!st_env || atoi(st_env) != 0) choose_small_tiles(P);
   }
   if (const char* tv = getenv("AAO_TIME_VARIANT")) {  // tuning override: "v64,v32,vff"
     int a = 0, b = -1;

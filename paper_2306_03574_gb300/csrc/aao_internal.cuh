@@ -68,6 +68,11 @@ constexpr int TIME_VARIANT_SMALL = 30;
 constexpr int DST_VARIANT_SMALL = 4;
 constexpr int SMALL_NT = 32;
 constexpr int small_pairs(int L) { return L >= 128 ? 1 : 128 / L; }
+// stencil / DST-basis operator kernels: threads per CTA (one spatial point each) and time
+// levels per thread run, standard and for small problems
+constexpr int YT_THREADS = 256;
+constexpr int YT_CH_STD = 32;
+constexpr int YT_CH_SMALL = 4;
 
 struct Plan {
   int d = 0, N = 0, M = 0, n = 0, m = 0, npairs = 0;
@@ -87,6 +92,11 @@ struct Plan {
   // pre-processing loads (aao_create: 1 for FP64 handles, 3 otherwise), or
   // DST_VARIANT_SMALL
   int dst_variant = 1;
+  // MINRES operator kernels: time levels per thread run of the stencil / DST-basis
+  // operator (32; small problems 4) and the small shape of the w/x update (8 modes x 16
+  // runs per CTA instead of 32 x 4), chosen with the small tiles
+  int yt_ch = 32;
+  int wx_small = 0;
   PrecTables<double> t64;
   PrecTables<float> t32;
   PrecTables<dfl> tff;  // double-float tables

@@ -16,8 +16,8 @@ namespace aao {
 
 namespace {
 
-constexpr int YT_NT = 256;
-constexpr int YT_CH = 32;
+constexpr int YT_NT = YT_THREADS;
+constexpr int YT_CH = YT_CH_STD;  // the grouped (serving) launches
 // Resident blocks per SM of the stencil kernels with a fused scalar step in their tail
 // (minres_scalars.cuh): the register budgets of the same kernels without it, so that the
 // step's registers (spilled if need be; it runs once per right-hand side) do not lower
@@ -29,6 +29,7 @@ constexpr int ytv_min_blocks(int D, int MODE) {
 
 struct YtArgs {
   int N, n, m;
+  int ch;  // time levels per thread run (Plan::yt_ch)
   double coef, diag;
 };
 
@@ -65,8 +66,8 @@ __device__ __forceinline__ void yt_run(const double* __restrict__ x, double* __r
                                        const YtArgs& a) {
   const int s = blockIdx.x * YT_NT + threadIdx.x;
   const int n = a.n, m = a.m, N = a.N;
-  const int i0 = blockIdx.y * YT_CH;
-  const int i1 = min(n, i0 + YT_CH);
+  const int i0 = blockIdx.y * a.ch;
+  const int i1 = min(n, i0 + a.ch);
   const long long rb = (long long)blockIdx.z * n * m;
   double acc = 0.0;
   if (s < m) {
@@ -128,10 +129,11 @@ __global__ void __launch_bounds__(YT_NT, yt_min_blocks(D, MODE))
 template <int MODE>
 __device__ __forceinline__ void ythat_body(const double* __restrict__ x, double* __restrict__ y,
                                            const double* __restrict__ w, double* __restrict__ part,
-                                           const double* __restrict__ lam, int n, int m, int bx, int by) {
+                                           const double* __restrict__ lam, int n, int m, int bx, int by,
+                                           int ch) {
   const int s = bx * YT_NT + threadIdx.x;
-  const int i0 = by * YT_CH;
-  const int i1 = min(n, i0 + YT_CH);
+  const int i0 = by * ch;
+  const int i1 = min(n, i0 + ch);
   double acc = 0.0;
   if (s < m) {
     const double ls = lam[s];
@@ -169,7 +171,7 @@ __device__ __forceinline__ void ythat_run(const double* __restrict__ x, double* 
   double* part = MODE != 0 ? partial + (long long)blockIdx.z * nb + (long long)blockIdx.y * gridDim.x + blockIdx.x
                            : nullptr;
   ythat_body<MODE>(x + rb, y ? y + rb : nullptr, w ? w + rb : nullptr, part, lam, a.n, a.m, blockIdx.x,
-                   blockIdx.y);
+                   blockIdx.y, a.ch);
 }
 
 template <int MODE>
@@ -194,27 +196,31 @@ __global__ void __launch_bounds__(YT_NT, 8)
 // DST basis (Section 3's stopping test on the system whose operator is pointwise in s):
 //   w_{j+1} = c0 z + c1 w_{j-1} + c2 w_j (written over w_{j-1}),   x += c3 w_{j+1},
 //   r_{n-1-i} = b_{n-1-i} - (Lambda_s (x_i + x_{i-2}) - 2 x_{i-1}),  partial = sum r^2,
-// with (c0..c3) = sc[rhs].cw.  A block owns WXR_S consecutive spatial modes and all n
-// time levels of them, split into WXR_C runs of n/WXR_C levels, one thread per mode
-// and run.  A run needs the updated x at the two levels before it, which the thread of
-// the previous run overwrites in place; every thread therefore recomputes those two
-// values (the same operations on the same inputs, so bit for bit the same) before a
-// barrier, and only then starts writing.  Converged right-hand sides (sc.done) are
-// left untouched and their partial is not written.
+// with (c0..c3) = sc[rhs].cw.  A block owns S consecutive spatial modes and all n time
+// levels of them, split into C runs of n/C levels, one thread per mode and run.  A run
+// needs the updated x at the two levels before it, which the thread of the previous
+// run overwrites in place; every thread therefore recomputes those two values (the
+// same operations on the same inputs, so bit for bit the same) before a barrier, and
+// only then starts writing.  Converged right-hand sides (sc.done) are left untouched
+// and their partial is not written.  Standard shape S = 32, C = 4; small problems
+// (fewer blocks than SMs) S = 8, C = 16: more blocks and shorter serial runs.
 constexpr int WXR_S = 32;
 constexpr int WXR_C = 4;
 constexpr int WXR_NT = WXR_S * WXR_C;
+constexpr int WXR_S_SMALL = 8;
+constexpr int WXR_C_SMALL = 16;
 
 // Block bx of one right-hand side (vectors point at it); partial sum to *part.
+template <int WS = WXR_S, int WC = WXR_C>
 __device__ __forceinline__ void wx_res_body(const double* __restrict__ z, double* __restrict__ wprev,
                                             const double* __restrict__ w, double* __restrict__ x,
                                             const double* __restrict__ b, const double* __restrict__ lam,
                                             const MinresScalars& S, double* __restrict__ part, int n, int m,
                                             int bx) {
   if (S.done) return;  // uniform over the block
-  const int s = bx * WXR_S + (int)(threadIdx.x % WXR_S);
-  const int len = n / WXR_C;
-  const int i0 = (int)(threadIdx.x / WXR_S) * len;
+  const int s = bx * WS + (int)(threadIdx.x % WS);
+  const int len = n / WC;
+  const int i0 = (int)(threadIdx.x / WS) * len;
   const bool on = s < m;
   const double c0 = S.cw[0], c1 = S.cw[1], c2 = S.cw[2], c3 = S.cw[3];
   const long long rb = s;
@@ -246,29 +252,33 @@ __device__ __forceinline__ void wx_res_body(const double* __restrict__ z, double
       x1 = xi;
     }
   }
-  const double t = block_sum<WXR_NT>(acc);
+  const double t = block_sum<WS * WC>(acc);
   if (threadIdx.x == 0) *part = t;
 }
 
-__global__ void __launch_bounds__(WXR_NT) k_wx_res(const double* __restrict__ z, double* __restrict__ wprev,
+template <int WS, int WC>
+__global__ void __launch_bounds__(WS * WC) k_wx_res(const double* __restrict__ z, double* __restrict__ wprev,
                                                    const double* __restrict__ w, double* __restrict__ x,
                                                    const double* __restrict__ b, const double* __restrict__ lam,
                                                    const MinresScalars* __restrict__ sc,
                                                    double* __restrict__ partial, int n, int m) {
   const long long rb = (long long)blockIdx.y * n * m;
   double* pr = partial + (long long)blockIdx.y * gridDim.x;
-  wx_res_body(z + rb, wprev + rb, w + rb, x + rb, b + rb, lam, sc[blockIdx.y], pr + blockIdx.x, n, m, blockIdx.x);
+  wx_res_body<WS, WC>(z + rb, wprev + rb, w + rb, x + rb, b + rb, lam, sc[blockIdx.y], pr + blockIdx.x, n, m,
+                      blockIdx.x);
 }
 
 // with the stop test (MINRES scalar step 3) in the tail
-__global__ void __launch_bounds__(WXR_NT, 12) k_wx_res_tail(const double* __restrict__ z, double* __restrict__ wprev,
+template <int WS, int WC>
+__global__ void __launch_bounds__(WS * WC, 12) k_wx_res_tail(const double* __restrict__ z, double* __restrict__ wprev,
                                                    const double* __restrict__ w, double* __restrict__ x,
                                                    const double* __restrict__ b, const double* __restrict__ lam,
                                                    const MinresScalars* __restrict__ sc,
                                                    double* __restrict__ partial, int n, int m, ScalarTail tl) {
   const long long rb = (long long)blockIdx.y * n * m;
   double* pr = partial + (long long)blockIdx.y * gridDim.x;
-  wx_res_body(z + rb, wprev + rb, w + rb, x + rb, b + rb, lam, sc[blockIdx.y], pr + blockIdx.x, n, m, blockIdx.x);
+  wx_res_body<WS, WC>(z + rb, wprev + rb, w + rb, x + rb, b + rb, lam, sc[blockIdx.y], pr + blockIdx.x, n, m,
+                      blockIdx.x);
   scalar_tail(tl, blockIdx.y, pr, gridDim.x, gridDim.x);
 }
 
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(YT_NT) k_g_ythat(const GroupRound* __restrict_
   if (P.sc->done) return;
   const int lb = blockIdx.x - g->yt[r];
   const int bx = lb % P.yt_gx, by = lb / P.yt_gx;
-  ythat_body<1>(P.z, P.T, P.z, P.partial + lb, P.lam, P.n, P.m, bx, by);
+  ythat_body<1>(P.z, P.T, P.z, P.partial + lb, P.lam, P.n, P.m, bx, by, YT_CH);
 }
 
 // the w/x update fused with the true residual for every problem
@@ -296,6 +306,7 @@ __global__ void __launch_bounds__(WXR_NT) k_g_wx_res(const GroupRound* __restric
 // (face arrays concatenated by axis; axis ax has N+1 faces along ax, N along the others).
 struct VarArgs {
   int N, n, m, d;
+  int ch;  // time levels per thread run (Plan::yt_ch)
   double cv;
   const double* face;  // d * (N+1) * N^(d-1)
 };
@@ -379,8 +390,8 @@ __device__ __forceinline__ void yt_var_run(const double* __restrict__ x, double*
                                            const VarArgs& a) {
   const int s = blockIdx.x * YT_NT + threadIdx.x;
   const int n = a.n, m = a.m, N = a.N;
-  const int i0 = blockIdx.y * YT_CH;
-  const int i1 = min(n, i0 + YT_CH);
+  const int i0 = blockIdx.y * a.ch;
+  const int i1 = min(n, i0 + a.ch);
   const long long rb = (long long)blockIdx.z * n * m;
   double acc = 0.0;
   if (s < m) {
@@ -493,6 +504,7 @@ YtArgs make_args(const Plan& P) {
   a.N = P.N;
   a.n = P.n;
   a.m = P.m;
+  a.ch = P.yt_ch;
   a.coef = P.coef;
   a.diag = 1.0 + 2.0 * P.d * P.coef;
   return a;
@@ -500,7 +512,10 @@ YtArgs make_args(const Plan& P) {
 
 }  // namespace
 
-int wxres_blocks_per_rhs(const Plan& P) { return (P.m + WXR_S - 1) / WXR_S; }
+int wxres_blocks_per_rhs(const Plan& P) {
+  const int S = P.wx_small ? WXR_S_SMALL : WXR_S;
+  return (P.m + S - 1) / S;
+}
 
 int group_yt_tiles(int m) { return (m + YT_NT - 1) / YT_NT; }
 int group_yt_blocks(int n, int m) { return group_yt_tiles(m) * ((n + YT_CH - 1) / YT_CH); }
@@ -523,13 +538,18 @@ cudaError_t launch_wx_res(const Plan& P, const double* lam, const double* z, dou
   if (nl) ++*nl;
   const dim3 g(wxres_blocks_per_rhs(P), nrhs);
   if (nb) *nb = (int)g.x;
-  if (tail) k_wx_res_tail<<<g, WXR_NT, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m, *tail);
-  else k_wx_res<<<g, WXR_NT, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m);
+  constexpr int SS = WXR_S_SMALL, CS = WXR_C_SMALL;
+  if (P.wx_small && tail)
+    k_wx_res_tail<SS, CS><<<g, SS * CS, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m, *tail);
+  else if (P.wx_small) k_wx_res<SS, CS><<<g, SS * CS, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m);
+  else if (tail) k_wx_res_tail<WXR_S, WXR_C><<<g, WXR_NT, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m,
+                                                                 *tail);
+  else k_wx_res<WXR_S, WXR_C><<<g, WXR_NT, 0, s>>>(z, wprev_out, w, x, b, lam, sc, partial, P.n, P.m);
   return cudaGetLastError();
 }
 
 int yt_blocks_per_rhs(const Plan& P) {
-  return ((P.m + YT_NT - 1) / YT_NT) * ((P.n + YT_CH - 1) / YT_CH);
+  return ((P.m + YT_NT - 1) / YT_NT) * ((P.n + P.yt_ch - 1) / P.yt_ch);
 }
 
 template <int D>
@@ -546,7 +566,7 @@ cudaError_t launch_yt(const Plan& P, const double* x, double* y, const double* w
                       int mode, int nrhs, cudaStream_t s, uint64_t* nl, int* nb, const ScalarTail* tail) {
   if (nl) ++*nl;
   const YtArgs a = make_args(P);
-  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + P.yt_ch - 1) / P.yt_ch, nrhs);
   if (nb) *nb = (int)(g.x * g.y);
   const ScalarTail tl = tail ? *tail : ScalarTail{};
   switch (P.d) {
@@ -563,7 +583,7 @@ cudaError_t launch_ythat(const Plan& P, const double* lam, const double* x, doub
                         const ScalarTail* tail) {
   if (nl) ++*nl;
   const YtArgs a = make_args(P);
-  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + P.yt_ch - 1) / P.yt_ch, nrhs);
   if (nb) *nb = (int)(g.x * g.y);
   const ScalarTail tl = tail ? *tail : ScalarTail{};
   if (mode == 0) k_ythat<0><<<g, YT_NT, 0, s>>>(x, y, w, partial, lam, a);
@@ -582,6 +602,7 @@ static VarArgs make_var(const Plan& P, const double* face) {
   a.n = P.n;
   a.m = P.m;
   a.d = P.d;
+  a.ch = P.yt_ch;
   a.cv = P.tau * P.tau / (2.0 * P.h * P.h);
   a.face = face;
   return a;
@@ -602,7 +623,7 @@ cudaError_t launch_yt_var(const Plan& P, const double* face, const double* x, do
                           const ScalarTail* tail) {
   if (nl) ++*nl;
   const VarArgs a = make_var(P, face);
-  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + YT_CH - 1) / YT_CH, nrhs);
+  dim3 g((P.m + YT_NT - 1) / YT_NT, (P.n + P.yt_ch - 1) / P.yt_ch, nrhs);
   if (nb) *nb = (int)(g.x * g.y);
   const ScalarTail tl = tail ? *tail : ScalarTail{};
   switch (P.d) {

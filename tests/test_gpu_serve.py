@@ -41,19 +41,19 @@ def _requests(k=24, seed=77):
 
 @contextlib.contextmanager
 def _standard_tiles():
-    """Served handles run their time pipelines in grouped launches with the standard
-    tiles (time variants 3 / 24 / 12), also where a handle alone would take the
-    small-problem tile: the solo reference solves are pinned to the same variants so
-    that their bits can be compared (read when the handle is created)."""
-    old = os.environ.get("AAO_TIME_VARIANT")
-    os.environ["AAO_TIME_VARIANT"] = "3,24,12"
+    """Served handles run their iterations in grouped launches with the standard tiles,
+    also where a handle alone would take the small-problem tiles: the solo reference
+    solves keep the standard tiles too (AAO_SMALL_TILES=0, read when the handle is
+    created) so that their bits can be compared."""
+    old = os.environ.get("AAO_SMALL_TILES")
+    os.environ["AAO_SMALL_TILES"] = "0"
     try:
         yield
     finally:
         if old is None:
-            del os.environ["AAO_TIME_VARIANT"]
+            del os.environ["AAO_SMALL_TILES"]
         else:
-            os.environ["AAO_TIME_VARIANT"] = old
+            os.environ["AAO_SMALL_TILES"] = old
 
 
 def _solo(p, rtol):

@@ -143,3 +143,34 @@ def test_dst_and_prec_variants(d, N, nt, monkeypatch):
                 s.apply_prec(xt, zt)
                 torch.cuda.synchronize()
                 assert relerr(zt.cpu().numpy(), ref_prec) < tol32, (dv, tv)
+
+
+@pytest.mark.parametrize("d,N,nt,nrhs", [(1, 63, 64, 1), (1, 255, 256, 2), (2, 63, 64, 1), (1, 511, 1024, 1)])
+def test_small_problem_tiles_solve(d, N, nt, nrhs, monkeypatch):
+    """Small problems take the small tiles by default (one-warp time and DST tiles,
+    operator runs of 4 time levels, the small w/x update shape); the solve reaches the
+    same true residual as with the standard tiles (AAO_SMALL_TILES=0), checked with the
+    oracle's operator, in the same number of iterations (+-1)."""
+    from oracle import system as OS
+    m = N ** d
+    tau = 1.0 / nt
+    x = W.random_field((nrhs, nt, m), seed=1900 + N + nt)
+    res = {}
+    for small in ("1", "0"):
+        monkeypatch.setenv("AAO_SMALL_TILES", small)
+        with aao.Solver(d, N, nt, tau, 1e-6, nrhs_max=nrhs, graph=True) as s:
+            xt = cu(x)
+            b = torch.empty_like(xt)
+            s.apply_op(xt, b)
+            y = torch.empty_like(xt)
+            st, info = s.solve(b, y, rtol=1e-10, maxit=100)
+            torch.cuda.synchronize()
+            assert st == aao.AAO_OK, (small, info)
+            res[small] = ([i["iters"] for i in info], b.cpu().numpy(), y.cpu().numpy())
+    for small, (it, b, y) in res.items():
+        for r in range(nrhs):
+            rel = np.linalg.norm(b[r] - OS.apply_YT(y[r], d, N, tau, 1.0)) / np.linalg.norm(b[r])
+            assert rel <= 1e-10 * 1.01, (small, r, rel)
+    assert all(abs(a - c) <= 1 for a, c in zip(res["1"][0], res["0"][0]))
+    assert np.abs(res["1"][2] - res["0"][2]).max() <= 1e-8 * np.abs(res["0"][2]).max()
+    assert aao.aao_wait_timeouts() == 0
