@@ -920,7 +920,16 @@ def run_profile_case(args):
             assert st == aao.AAO_OK, info
 
     if not args.sweep:
-        with aao.Solver(d, N, nt, 1.0 / nt, args.pc_alpha, precision=prec, nrhs_max=args.nrhs) as s:
+        # solves run host-driven (kernels of a graph with a WHILE node are not profiled)
+        kw = dict(precision=prec, nrhs_max=args.nrhs, graph=args.what != "solve")
+        if args.varcoef:  # Example 2's coefficient, mean-coefficient preconditioner
+            import workloads as W
+            afun = W.example2(N, nt).meta["a"]
+            kw.update(variable_coefficient=True, c2=W.grid_mean(afun, d, N))
+        with aao.Solver(d, N, nt, 1.0 / nt, args.pc_alpha, **kw) as s:
+            if args.varcoef:
+                s.set_coefficient(torch.from_numpy(np.concatenate(
+                    [fc.ravel() for fc in W.face_coefficients(afun, d, N)])).cuda())
             for _ in range(args.reps):
                 one(s)
             torch.cuda.synchronize()
@@ -928,7 +937,7 @@ def run_profile_case(args):
         return 0
     nvar = {"fp64": 8, "fp32": 30, "f32x2": 14}[args.precision]
     times = {}
-    for v in range(nvar):
+    for v in list(range(nvar)) + [30]:  # 30: the small-problem tile
         os.environ["AAO_TIME_VARIANT"] = f"{v},{v},{v}"
         with aao.Solver(d, N, nt, 1.0 / nt, args.pc_alpha, precision=prec, nrhs_max=args.nrhs) as s:
             one(s)
@@ -1028,6 +1037,7 @@ def main():
     pc.add_argument("--time-variant", type=int, default=None)
     pc.add_argument("--dst-variant", type=int, default=None)
     pc.add_argument("--sweep", action="store_true", help="time every time-kernel variant")
+    pc.add_argument("--varcoef", action="store_true", help="Example 2's variable coefficient (2D)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
