@@ -935,9 +935,9 @@ def run_profile_case(args):
             torch.cuda.synchronize()
         print("ok")
         return 0
-    nvar = {"fp64": 8, "fp32": 30, "f32x2": 14}[args.precision]
+    nvar = {"fp64": 8, "fp32": 34, "f32x2": 14}[args.precision]
     times = {}
-    for v in list(range(nvar)) + [30]:  # 30: the small-problem tile
+    for v in sorted(set(range(nvar)) | {30}):  # 30: the small-problem tile
         os.environ["AAO_TIME_VARIANT"] = f"{v},{v},{v}"
         with aao.Solver(d, N, nt, 1.0 / nt, args.pc_alpha, precision=prec, nrhs_max=args.nrhs) as s:
             one(s)

@@ -1147,7 +1147,8 @@ const char* aao_last_error(void) { return g_err.c_str(); }
 // other number is folded onto the range the mode has).
 static int clamp_time_variant(int v, int prec) {
   if (v == TIME_VARIANT_SMALL) return v;
-  return v & (prec == AAO_PREC_FP64 ? 7 : prec == AAO_PREC_F32X2 ? 15 : 31);
+  if (prec == AAO_PREC_FP32_IR) return v >= 0 && v < 34 ? v : v & 31;
+  return v & (prec == AAO_PREC_FP64 ? 7 : 15);
 }
 static int clamp_dst_variant(int v) { return v == DST_VARIANT_SMALL ? v : v & 3; }
 
@@ -1406,10 +1407,12 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // conversions; 18..21: with batched loads; 22, 23: 18, 19 with the spectral table
   // computed on the fly instead of read; 24..29: 18, 19 with the store, load or both
   // conversions by integer operations)
-  // conversions by integer operations); every mode also has the small tile
-  const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 30 : 8;
+  // conversions by integer operations; 31..33: 27, 29, 26 without the staged table
+  // slice); every mode also has the small tile (30)
+  const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 34 : 8;
   std::vector<int> tvs, dvs = {0, 1, 2, 3, DST_VARIANT_SMALL};
-  for (int v = 0; v < ntv; ++v) tvs.push_back(v);
+  for (int v = 0; v < ntv; ++v)
+    if (v != TIME_VARIANT_SMALL) tvs.push_back(v);
   tvs.push_back(TIME_VARIANT_SMALL);
   auto pick = [](const std::vector<int>& vs, const std::vector<float>& t, int def) {
     size_t b = 0, d = 0;

@@ -366,6 +366,11 @@ static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrh
     if (v == 27) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 1, 8>(P, in, out, nrhs, s);
     if (v == 28) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, -1, 3, 8>(P, in, out, nrhs, s);
     if (v == 29) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, -1, 3, 8>(P, in, out, nrhs, s);
+    // 31, 32 = 27, 29 and 33 = 26 without the staged table slice (the mix passes read the
+    // table from memory): half the shared memory, more CTAs per SM
+    if (v == 31) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, 0, 1, 8>(P, in, out, nrhs, s);
+    if (v == 32) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, 0, 3, 8>(P, in, out, nrhs, s);
+    if (v == 33) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, 0, 1, 8>(P, in, out, nrhs, s);
   }
   if constexpr (std::is_same<R, dfl>::value) {
     // 12, 13 = variants 9, 11 with the loads batched 8 tasks at a time

@@ -60,8 +60,9 @@ def test_time_variants(d, N, nt, monkeypatch):
     # FP32 on FP64 vectors: 8..15 bulk-staged tile, 16, 17 integer conversions, 18..21
     # loads batched ahead of their conversion, 22, 23 spectral table computed on the fly,
     # 24..29 batched loads with integer conversions of the stores, the loads or both;
-    # 30 the one-warp small-problem tile (every precision)
-    for v in list(range(30)) + [30]:
+    # 30 the one-warp small-problem tile (every precision); 31..33 without the staged
+    # table slice
+    for v in range(34):
         monkeypatch.setenv("AAO_TIME_VARIANT", f"{v if v == 30 else v & 7},{v}")
         both = v < 8 or v == 30
         for prec in (aao.AAO_PREC_FP64, aao.AAO_PREC_FP32_IR) if both else (aao.AAO_PREC_FP32_IR,):
@@ -94,7 +95,7 @@ def test_bulk_staged_time_kernel_guards_and_alignment(d, N, nt, monkeypatch):
     x = W.random_field((nt, m), seed=1750 + nt + N)
     ref = _time_ref(d, N, nt, x)
     tol32 = gates.fp32("time", d, N, nt, ALPHA)
-    for v in list(range(8, 16)) + list(range(18, 30)):
+    for v in list(range(8, 16)) + list(range(18, 30)) + [31, 32, 33]:
         monkeypatch.setenv("AAO_TIME_VARIANT", f"3,{v}")
         with aao.Solver(d, N, nt, 1.0 / nt, ALPHA, precision=aao.AAO_PREC_FP32_IR) as s:
             xt = guards.guarded_copy(x)
