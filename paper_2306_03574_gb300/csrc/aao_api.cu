@@ -111,6 +111,7 @@ struct aao_handle {
   // host-solve staging (allocated on first aao_solve_host)
   double* hs_f = nullptr; double* hs_psi = nullptr; double* hs_b = nullptr; double* hs_x = nullptr;
   cudaStream_t hs_copy = nullptr;    // copy stream of the pipelined host-buffer solve
+  cudaStream_t hs_work[2] = {nullptr, nullptr};  // its two chunk-compute streams
   std::vector<cudaEvent_t> hs_ev;    // its chunk events (created on first use)
   // serving: pinned host staging of an asynchronous re-bind (aaoi_serving_prepare)
   void* pin = nullptr;
@@ -141,6 +142,8 @@ struct aao_handle {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (own_stream) cudaStreamDestroy(own_stream);
     if (hs_copy) cudaStreamDestroy(hs_copy);
+    for (cudaStream_t w : hs_work)
+      if (w) cudaStreamDestroy(w);
     for (cudaEvent_t e : hs_ev) cudaEventDestroy(e);
     clear_prof();
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -249,8 +252,8 @@ aao_status check_call(aao_handle* h, int nrhs) {
 }
 
 // Device buffers of aao_solve_host (f, b, x, psi0 and psi1 for nrhs_max right-hand
-// sides), its copy stream and its chunk events: reserved by aao_create when
-// opts.host_staging is set, else by the first aao_solve_host.
+// sides), its copy stream, two chunk-compute streams and its events: reserved by
+// aao_create when opts.host_staging is set, else by the first aao_solve_host.
 constexpr int HOST_CHUNK = 32;  // time levels per pipelined copy chunk (n is a power of two >= 64)
 aao_status reserve_host_staging(aao_handle* h) {
   const size_t vl = (size_t)h->nrhs_max * h->vlen();
@@ -259,8 +262,9 @@ aao_status reserve_host_staging(aao_handle* h) {
   AAO_TRY(h->alloc(&h->hs_x, vl));
   AAO_TRY(h->alloc(&h->hs_psi, (size_t)2 * h->nrhs_max * h->P.m));
   AAO_CK(cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking));
+  for (cudaStream_t& w : h->hs_work) AAO_CK(cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking));
   const int nch = h->nrhs_max * (h->P.n / HOST_CHUNK);
-  while ((int)h->hs_ev.size() < 2 * nch + 2) {
+  while ((int)h->hs_ev.size() < 2 * nch + 8) {
     cudaEvent_t e = nullptr;
     AAO_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     h->hs_ev.push_back(e);
@@ -1608,7 +1612,9 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
   // levels, so the upload of f overlaps the right-hand side and the forward DSTs of the
   // chunks already there, and the download of x overlaps the inverse DSTs of later
   // chunks.  Every level of the right-hand side and of the DSTs depends on its own f
-  // level (and psi0, psi1) only, so chunking changes no value.
+  // level (and psi0, psi1) only, so chunking changes no value.  The chunks' kernels
+  // alternate between two streams: one chunk's DST grid fills only part of the GPU, and
+  // two chunks side by side keep it busy.
   const int CH = HOST_CHUNK;
   const int per = P.n / CH, nch = nrhs * per;
   const size_t lb = (size_t)P.m * sizeof(double);
@@ -1623,26 +1629,45 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
     AAO_CK(cudaMemcpyAsync(h->hs_f + off, f + off, CH * lb, cudaMemcpyHostToDevice, cs));
     AAO_CK(cudaEventRecord(ev[c], cs));
   }
+  cudaStream_t* ws = h->hs_work;
+  auto fork = [&](cudaEvent_t e) -> aao_status {  // both work streams follow s
+    AAO_CK(cudaEventRecord(e, s));
+    for (int i = 0; i < 2; ++i) AAO_CK(cudaStreamWaitEvent(ws[i], e, 0));
+    return AAO_OK;
+  };
+  auto join = [&](cudaEvent_t e0, cudaEvent_t e1) -> aao_status {  // s follows both
+    AAO_CK(cudaEventRecord(e0, ws[0]));
+    AAO_CK(cudaEventRecord(e1, ws[1]));
+    AAO_CK(cudaStreamWaitEvent(s, e0, 0));
+    AAO_CK(cudaStreamWaitEvent(s, e1, 0));
+    return AAO_OK;
+  };
+  AAO_TRY(fork(ev[2 * nch + 2]));
   for (int c = 0; c < nch; ++c) {
     const int r = c / per, k0 = (c % per) * CH;
     const size_t rb = (size_t)r * P.n * P.m;
-    AAO_CK(cudaStreamWaitEvent(s, ev[c], 0));
-    AAO_KL(h, KC_RHS, s, launch_build_rhs_levels(P, h->hs_f + rb, d_psi0 + (size_t)r * P.m,
-                                                 d_psi1 + (size_t)r * P.m, h->hs_b + rb, k0, CH, s,
+    cudaStream_t w = ws[c & 1];
+    AAO_CK(cudaStreamWaitEvent(w, ev[c], 0));
+    AAO_KL(h, KC_RHS, w, launch_build_rhs_levels(P, h->hs_f + rb, d_psi0 + (size_t)r * P.m,
+                                                 d_psi1 + (size_t)r * P.m, h->hs_b + rb, k0, CH, w,
                                                  &h->launches));
     const size_t bo = rb + (size_t)(P.n - k0 - CH) * P.m;  // the b levels this chunk filled
-    AAO_TRY(dst_apply_levels(h, h->hs_b + bo, h->vbh + bo, CH, s));
+    AAO_TRY(dst_apply_levels(h, h->hs_b + bo, h->vbh + bo, CH, w));
   }
+  AAO_TRY(join(ev[2 * nch + 3], ev[2 * nch + 4]));
   std::vector<aao_solve_info> loc(nrhs);
   aao_solve_info* inf = info ? info : loc.data();
   aao_status worst = minres_spectral(h, h->vbh, h->vxh, 0, nrhs, rtol, maxit, inf, s, true);
+  AAO_TRY(fork(ev[2 * nch + 5]));
   for (int c = 0; c < nch; ++c) {
     const size_t off = (size_t)(c / per) * P.n * P.m + (size_t)(c % per) * CH * P.m;
-    AAO_TRY(dst_apply_levels(h, h->vxh + off, h->hs_x + off, CH, s));
-    AAO_CK(cudaEventRecord(ev[nch + c], s));
+    cudaStream_t w = ws[c & 1];
+    AAO_TRY(dst_apply_levels(h, h->vxh + off, h->hs_x + off, CH, w));
+    AAO_CK(cudaEventRecord(ev[nch + c], w));
     AAO_CK(cudaStreamWaitEvent(cs, ev[nch + c], 0));
     AAO_CK(cudaMemcpyAsync(u + off, h->hs_x + off, CH * lb, cudaMemcpyDeviceToHost, cs));
   }
+  AAO_TRY(join(ev[2 * nch + 6], ev[2 * nch + 7]));
   AAO_TRY(physical_check(h, h->hs_b, h->hs_x, nrhs, rtol, inf, &worst, s));
   AAO_CK(cudaEventRecord(ev[2 * nch + 1], cs));  // the caller's stream ends after the copies
   AAO_CK(cudaStreamWaitEvent(s, ev[2 * nch + 1], 0));
