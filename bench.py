@@ -935,7 +935,7 @@ def run_profile_case(args):
             torch.cuda.synchronize()
         print("ok")
         return 0
-    nvar = {"fp64": 8, "fp32": 34, "f32x2": 14}[args.precision]
+    nvar = {"fp64": 8, "fp32": 34, "f32x2": 15}[args.precision]
     times = {}
     for v in sorted(set(range(nvar)) | {30}):  # 30: the small-problem tile
         os.environ["AAO_TIME_VARIANT"] = f"{v},{v},{v}"

@@ -1413,7 +1413,7 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // conversions by integer operations)
   // conversions by integer operations; 31..33: 27, 29, 26 without the staged table
   // slice); every mode also has the small tile (30)
-  const int ntv = prec == AAO_PREC_F32X2 ? 14 : prec == AAO_PREC_FP32_IR ? 34 : 8;
+  const int ntv = prec == AAO_PREC_F32X2 ? 15 : prec == AAO_PREC_FP32_IR ? 34 : 8;
   std::vector<int> tvs, dvs = {0, 1, 2, 3, DST_VARIANT_SMALL};
   for (int v = 0; v < ntv; ++v)
     if (v != TIME_VARIANT_SMALL) tvs.push_back(v);

@@ -313,9 +313,18 @@ __global__ void __launch_bounds__(NT) k_time(const TIO* in, TIO* out, TimeArgs a
   time_body<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD, OTF>(in + rb, out + rb, a, tb, blockIdx.x);
 }
 
+// The same built for MINB resident CTAs per SM (a register cap; the spills it may cause
+// are the price of the occupancy)
+template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG, int ICVT, int PRELOAD,
+          bool OTF, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_time_occ(const TIO* in, TIO* out, TimeArgs a, PrecTables<R> tb) {
+  const long long rb = (long long)blockIdx.y * L * a.m;
+  time_body<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD, OTF>(in + rb, out + rb, a, tb, blockIdx.x);
+}
+
 // Tile shapes: full = 4096/L modes-pairs x 256 threads, half = 2048/L x 128 threads.
 template <typename R, typename TIO, int L, int NS, int NT, int FFTV, int LAY, int STG = -1, int ICVT = 0,
-          int PRELOAD = 0, bool OTF = false>
+          int PRELOAD = 0, bool OTF = false, int MINB = 0>
 static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int nrhs, cudaStream_t s) {
   using C = typename Cplx<R>::T;
   constexpr bool STAGED = STG < 0 ? LAY == 1 : STG == 1;
@@ -325,10 +334,13 @@ static cudaError_t time_launch_cfg(const Plan& P, const TIO* in, TIO* out, int n
   a.m = P.m;
   a.n = P.n;
   a.npairs = P.npairs;
-  auto kern = k_time<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD, OTF>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntile = (P.m + 2 * NS - 1) / (2 * NS);
-  kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<dim3(ntile, nrhs), NT, smem, s>>>(in, out, a, tables<R>(P));
+  };
+  if constexpr (MINB > 0) go(k_time_occ<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD, OTF, MINB>);
+  else go(k_time<R, TIO, L, NS, NT, FFTV, LAY, STG, ICVT, PRELOAD, OTF>);
   return cudaGetLastError();
 }
 
@@ -376,6 +388,9 @@ static cudaError_t time_launch_L(const Plan& P, const TIO* in, TIO* out, int nrh
     // 12, 13 = variants 9, 11 with the loads batched 8 tasks at a time
     if (v == 12) return time_launch_cfg<R, TIO, L, 4096 / L, 256, 1, 1, 0, 0, 8>(P, in, out, nrhs, s);
     if (v == 13) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, 0, 0, 8>(P, in, out, nrhs, s);
+    // 14 = 13 built for 5 CTAs per SM (the half tile's shared memory allows 5, its 120
+    // registers 4)
+    if (v == 14) return time_launch_cfg<R, TIO, L, 2048 / L, 128, 1, 1, 0, 0, 8, false, 5>(P, in, out, nrhs, s);
     if (v & 8) {  // interleaved layout without the staged table slice
       switch (v & 3) {
         case 0: return time_launch_cfg<R, TIO, L, 4096 / L, 256, 0, 1, 0>(P, in, out, nrhs, s);

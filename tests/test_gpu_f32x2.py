@@ -68,8 +68,8 @@ def test_f32x2_time_variants(d, N, nt, monkeypatch):
     x = W.random_field((nt, m), seed=2400 + nt)
     ref = OF.time_part_modes(d, N, nt, tau, alpha, x, np.arange(m))
     # 8..11: interleaved layout without the staged table slice; 12, 13 batched loads;
-    # 30 the one-warp small-problem tile
-    for v in list(range(14)) + [30]:
+    # 14: 13 built for 5 CTAs per SM; 30 the one-warp small-problem tile
+    for v in list(range(15)) + [30]:
         monkeypatch.setenv("AAO_TIME_VARIANT", f"{v},{v},{v}")
         with aao.Solver(d, N, nt, tau, alpha, precision=aao.AAO_PREC_F32X2) as s:
             xt = cu(x)
