@@ -937,8 +937,14 @@ def run_profile_case(args):
         return 0
     nvar = {"fp64": 8, "fp32": 34, "f32x2": 15}[args.precision]
     times = {}
-    for v in sorted(set(range(nvar)) | {30}):  # 30: the small-problem tile
-        os.environ["AAO_TIME_VARIANT"] = f"{v},{v},{v}"
+    # --what dst sweeps the DST variants (8: the small-problem tile), else the time
+    # kernel's (30: the small-problem tile)
+    sweep = range(9) if args.what == "dst" else sorted(set(range(nvar)) | {30})
+    for v in sweep:
+        if args.what == "dst":
+            os.environ["AAO_DST_VARIANT"] = str(v)
+        else:
+            os.environ["AAO_TIME_VARIANT"] = f"{v},{v},{v}"
         with aao.Solver(d, N, nt, 1.0 / nt, args.pc_alpha, precision=prec, nrhs_max=args.nrhs) as s:
             one(s)
             torch.cuda.synchronize()

@@ -126,8 +126,9 @@ typedef struct aao_handle aao_handle;
  * Tuning overrides (environment, read here; for measurements and tests):
  *   AAO_TIME_VARIANT="v64[,v32[,vff]]" sets the time-kernel variant per precision
  *   (the numbering of aao_autotune; a missing entry repeats the previous one), and
- *   AAO_DST_VARIANT="0..4" the DST variant (bit 0: radix-16-first stage plan, bit 1:
- *   batched loads; 4: the one-warp small-problem tile), AAO_SMALL_TILES=0 keeps the
+ *   AAO_DST_VARIANT="0..8" the DST variant (bit 0: radix-16-first stage plan, bit 1:
+ *   batched loads, bit 2: interleaved padded shared-memory layout; 8: the one-warp
+ *   small-problem tile), AAO_SMALL_TILES=0 keeps the
  *   standard tiles for a small problem (by default a problem whose standard tiles
  *   would occupy fewer than a quarter of the SMs gets the one-warp time (variant 30)
  *   and DST tiles, operator runs of 4 time levels and the small w/x update shape;
@@ -351,7 +352,8 @@ const char* aao_serve_last_error(void);
  * conversion, bulk-copy staging of the tile or integer conversions (of the loads, the
  * stores or both), and, in FP32, the spectral table read from memory or computed on
  * the fly) and of the DST
- * kernel (radix-4 or radix-16 stage plan, with or without batched loads) by timing
+ * kernel (radix-4 or radix-16 stage plan, with or without batched loads, sequence-major
+ * or interleaved shared-memory layout, or the small-problem tile) by timing
  * each on the handle's workspace with CUDA events (the work of the kernels is
  * the same in every variant; only speed differs).  The default variant is kept unless
  * another is more than 1 % faster, so near-ties give the same choice on every run.

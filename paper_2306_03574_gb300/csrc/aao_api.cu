@@ -953,6 +953,12 @@ aao_status aaoi_solve_enqueue(aao_handle* h, const double* b, double* x, double 
   return AAO_OK;
 }
 
+// DST default: the FP64 DST is bound by the FP64 pipe (radix-16 plan; the other axes
+// change nothing); the double-float DSTs (the handle's DSTs in the other modes) gain from
+// batched loads and the interleaved shared-memory layout (measured on GB300: 0.660 ->
+// 0.622 ms for both axes at 255^2 x 256, 5.02 -> 4.56 ms at 511^2 x 512).
+static int default_dst_variant(int precision) { return precision == AAO_PREC_FP64 ? 1 : 7; }
+
 // Small problems: where the standard tiles give fewer CTAs than a quarter of the 152
 // SMs, kernels with smaller tiles spread the work wider (1D 63 x 64: the time pipeline
 // and the DST run on 16 CTAs instead of 1, the operator on 16 instead of 2): the
@@ -976,7 +982,7 @@ static void use_standard_tiles(Plan& P, int precision) {
   if (P.time_variant64 == TIME_VARIANT_SMALL) P.time_variant64 = standard.time_variant64;
   if (P.time_variant32 == TIME_VARIANT_SMALL) P.time_variant32 = standard.time_variant32;
   if (P.time_variant_ff == TIME_VARIANT_SMALL) P.time_variant_ff = standard.time_variant_ff;
-  if (P.dst_variant == DST_VARIANT_SMALL) P.dst_variant = precision == AAO_PREC_FP64 ? 1 : 3;
+  if (P.dst_variant == DST_VARIANT_SMALL) P.dst_variant = default_dst_variant(precision);
   P.yt_ch = standard.yt_ch;
   P.wx_small = standard.wx_small;
 }
@@ -1154,7 +1160,7 @@ static int clamp_time_variant(int v, int prec) {
   if (prec == AAO_PREC_FP32_IR) return v >= 0 && v < 34 ? v : v & 31;
   return v & (prec == AAO_PREC_FP64 ? 7 : 15);
 }
-static int clamp_dst_variant(int v) { return v == DST_VARIANT_SMALL ? v : v & 3; }
+static int clamp_dst_variant(int v) { return v == DST_VARIANT_SMALL ? v : v & 7; }
 
 aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aao_scheme scheme,
                       const aao_opts* opts, aao_handle** out) {
@@ -1205,9 +1211,7 @@ aao_status aao_create(const aao_grid* grid, int nt, double tau, double alpha, aa
   P.c2 = grid->c2;
   P.h = 1.0 / (double)M;
   P.coef = P.c2 * tau * tau / (2.0 * P.h * P.h);
-  // DST default: the FP64 DST is bound by the FP64 pipe; the double-float and FP32 DSTs
-  // (the handle's DSTs in the other modes) gain from batched loads (measured on GB300)
-  P.dst_variant = o.precision == AAO_PREC_FP64 ? 1 : 3;
+  P.dst_variant = default_dst_variant(o.precision);
   {
     const char* st_env = getenv("AAO_SMALL_TILES");
     if (!st_env || atoi(st_env) != 0) choose_small_tiles(P);
@@ -1414,7 +1418,7 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   // conversions by integer operations; 31..33: 27, 29, 26 without the staged table
   // slice); every mode also has the small tile (30)
   const int ntv = prec == AAO_PREC_F32X2 ? 15 : prec == AAO_PREC_FP32_IR ? 34 : 8;
-  std::vector<int> tvs, dvs = {0, 1, 2, 3, DST_VARIANT_SMALL};
+  std::vector<int> tvs, dvs = {0, 1, 2, 3, 4, 5, 6, 7, DST_VARIANT_SMALL};
   for (int v = 0; v < ntv; ++v)
     if (v != TIME_VARIANT_SMALL) tvs.push_back(v);
   tvs.push_back(TIME_VARIANT_SMALL);

@@ -65,7 +65,7 @@ struct PrecTables {
 // line pairs (DST) the radix-4 stage plan allows (128/L, at least 1), so that a problem
 // of a few thousand unknowns spreads over tens of SMs instead of one CTA.
 constexpr int TIME_VARIANT_SMALL = 30;
-constexpr int DST_VARIANT_SMALL = 4;
+constexpr int DST_VARIANT_SMALL = 8;
 constexpr int SMALL_NT = 32;
 constexpr int small_pairs(int L) { return L >= 128 ? 1 : 128 / L; }
 // stencil / DST-basis operator kernels: threads per CTA (one spatial point each) and time
@@ -89,8 +89,8 @@ struct Plan {
   // default when the standard tiles would leave most SMs idle).
   int time_variant64 = 3, time_variant32 = 24, time_variant_ff = 12;
   // DST variant: bit 0 = radix-16-first stage plan (else radix-4), bit 1 = batched
-  // pre-processing loads (aao_create: 1 for FP64 handles, 3 otherwise), or
-  // DST_VARIANT_SMALL
+  // pre-processing loads, bit 2 = interleaved padded shared-memory layout (aao_create:
+  // 1 for FP64 handles, 7 otherwise), or DST_VARIANT_SMALL
   int dst_variant = 1;
   // MINRES operator kernels: time levels per thread run of the stencil / DST-basis
   // operator (32; small problems 4) and the small shape of the w/x update (8 modes x 16

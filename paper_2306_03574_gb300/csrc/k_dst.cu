@@ -38,16 +38,21 @@ struct DstArgs {
 
 // PRE: the pre-processing loads of a thread issued in batches of 4 tasks (16 values)
 // before any of them is used, the first batch ahead of the table loads and the barrier.
-template <typename R, typename TIO, int M, int NS, int NT, bool STRIDED, int FFTV, bool PRE = false>
+// LAY: shared-memory layout of the line pairs (fft_smem.cuh: 0 sequence-major, 1
+// interleaved and padded); with LAY 1 the threads of a warp walk the line pairs first in
+// the pre-processing and the store too, so that their shared-memory accesses stay
+// conflict-free (the global accesses then take whole 32-byte sectors of several lines).
+template <typename R, typename TIO, int M, int NS, int NT, bool STRIDED, int FFTV, bool PRE = false, int LAY = 0>
 __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, PrecTables<R> tb) {
   using C = typename Cplx<R>::T;
+  using Y = SLay<M, NS, LAY>;
   constexpr int H = M / 2;
   constexpr int TPS = NT / NS;     // threads per line pair in the post-processing
   constexpr int KQ = H / TPS;      // k values per thread
   static_assert(NT % NS == 0 && H % TPS == 0 && TPS <= 32 && (32 % TPS) == 0, "dst config");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* cbuf = reinterpret_cast<C*>(smem_raw);
-  C* tw = cbuf + NS * M;
+  C* tw = cbuf + Y::size;
   R* sw = reinterpret_cast<R*>(tw + M);
 
   const int tid = threadIdx.x;
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
   // ---- pre-processing: y'_j, y'_{M-j} for j = 1..M/2 of lines a, b ----
   // task -> (line pair q, index j); the four inputs x_j, x_{M-j} of lines a, b
   auto task_qj = [&](int task, int& q, int& j) {
-    if (!STRIDED) { q = task / H; j = task % H + 1; }
+    if (!STRIDED && !LAY) { q = task / H; j = task % H + 1; }
     else { q = task % NS; j = task / NS + 1; }
   };
   auto load4 = [&](int task, TIO& a0, TIO& a1, TIO& b0, TIO& b1) {
@@ -108,8 +113,8 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
     C lo, hi;
     lo.x = fmadd(w, sa, ta);  lo.y = fmadd(w, sb, tbb);
     hi.x = fmadd(w, sa, -ta); hi.y = fmadd(w, sb, -tbb);
-    cbuf[q * M + j] = lo;
-    if (j != H) cbuf[q * M + M - j] = hi;
+    cbuf[Y::at(q, j)] = lo;
+    if (j != H) cbuf[Y::at(q, M - j)] = hi;
   };
   if constexpr (PRE) {
     constexpr int TPT = NS * H / NT, PB = 4;
@@ -139,11 +144,11 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
       weigh(task, R(a0), R(a1), R(b0), R(b1));
     }
   }
-  for (int q = tid; q < NS; q += NT) { C z; z.x = R(); z.y = R(); cbuf[q * M] = z; }
+  for (int q = tid; q < NS; q += NT) { C z; z.x = R(); z.y = R(); cbuf[Y::at(q, 0)] = z; }
   __syncthreads();
 
-  if constexpr (FFTV == 0) fft_block<M, NS, NT, false>(cbuf, tw);
-  else fft_block16<M, NS, NT, false>(cbuf, tw);
+  if constexpr (FFTV == 0) fft_block<M, NS, NT, false, LAY>(cbuf, tw);
+  else fft_block16<M, NS, NT, false, LAY>(cbuf, tw);
 
   // ---- post-processing: separate the two lines, prefix sum for odd outputs ----
   const int q = tid / TPS, lq = tid % TPS;
@@ -154,12 +159,12 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
 #pragma unroll
     for (int i = 0; i < KQ; ++i) {
       const int k = k0 + i;
-      const C ck = cbuf[q * M + k];
+      const C ck = cbuf[Y::at(q, k)];
       R ra, rb;
       if (k == 0) {
         ra = ck.x; rb = ck.y; ia[i] = R(); ib[i] = R();
       } else {
-        const C cm = cbuf[q * M + M - k];
+        const C cm = cbuf[Y::at(q, M - k)];
         ra = ck.x + cm.x; rb = ck.y + cm.y;
         ia[i] = cm.y - ck.y; ib[i] = ck.x - cm.x;
       }
@@ -183,16 +188,26 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
   for (int i = 0; i < KQ; ++i) {
     const int k = k0 + i;
     C odd; odd.x = pa[i] + ex_a; odd.y = pb[i] + ex_b;
-    cbuf[q * M + 2 * k] = odd;            // X_{2k+1} -> index 2k
+    cbuf[Y::at(q, 2 * k)] = odd;          // X_{2k+1} -> index 2k
     if (k >= 1) {
       C ev; ev.x = ia[i]; ev.y = ib[i];
-      cbuf[q * M + 2 * k - 1] = ev;       // X_{2k}   -> index 2k-1
+      cbuf[Y::at(q, 2 * k - 1)] = ev;     // X_{2k}   -> index 2k-1
     }
   }
   __syncthreads();
 
   // ---- store ----
-  if (!STRIDED) {
+  if (!STRIDED && LAY) {
+    // lines fastest across the threads (conflict-free reads of the interleaved layout)
+    const long long e0 = line0 * N;
+    for (int task = tid; task < 2 * NS * N; task += NT) {
+      const int l = task % (2 * NS), j = task / (2 * NS);
+      if (line0 + l < a.nlines) {
+        const C v = cbuf[Y::at(l >> 1, j)];
+        out[e0 + (long long)l * N + j] = TIO((l & 1) ? v.y : v.x);
+      }
+    }
+  } else if (!STRIDED) {
     // line by line (no division by the runtime length N); rows are contiguous in memory
     const long long e0 = line0 * N;
     for (int l = 0; l < 2 * NS; ++l) {
@@ -209,7 +224,7 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
       const int l = task % (2 * NS), j = task / (2 * NS);
       const int il = i0 + l;
       if (il < a.st) {
-        const C v = cbuf[(l >> 1) * M + j];
+        const C v = cbuf[Y::at(l >> 1, j)];
         out[obase + (long long)j * a.st + il] = TIO((l & 1) ? v.y : v.x);
       }
     }
@@ -217,12 +232,12 @@ __global__ void __launch_bounds__(NT) k_dst(const TIO* in, TIO* out, DstArgs a, 
 }
 
 // NS line pairs per CTA of NT threads (standard: 2048/M pairs, 128 threads)
-template <typename R, typename TIO, int M, int FFTV, bool PRE, int NS = 2048 / M, int NT = 128>
+template <typename R, typename TIO, int M, int FFTV, bool PRE, int NS = 2048 / M, int NT = 128, int LAY = 0>
 static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs,
                                  cudaStream_t s) {
   using C = typename Cplx<R>::T;
   const PrecTables<R>& tb = tables<R>(P);
-  const size_t smem = sizeof(C) * (NS * M + M) + sizeof(R) * (M / 2 + 1);
+  const size_t smem = sizeof(C) * (SLay<M, NS, LAY>::size + M) + sizeof(R) * (M / 2 + 1);
   DstArgs a;
   a.N = P.N;
   long long stride = 1;
@@ -232,7 +247,7 @@ static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axi
     a.nlines = total / P.N;
     a.st = 1;
     a.nouter = 0;
-    auto kern = k_dst<R, TIO, M, NS, NT, false, FFTV, PRE>;
+    auto kern = k_dst<R, TIO, M, NS, NT, false, FFTV, PRE, LAY>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const long long nb = (a.nlines + 2 * NS - 1) / (2 * NS);
     kern<<<dim3((unsigned)nb), NT, smem, s>>>(in, out, a, tb);
@@ -240,7 +255,7 @@ static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axi
     a.st = (int)stride;
     a.nouter = total / (stride * P.N);
     a.nlines = 0;
-    auto kern = k_dst<R, TIO, M, NS, NT, true, FFTV, PRE>;
+    auto kern = k_dst<R, TIO, M, NS, NT, true, FFTV, PRE, LAY>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int ntile = (int)((stride + 2 * NS - 1) / (2 * NS));
     kern<<<dim3((unsigned)a.nouter, (unsigned)ntile), NT, smem, s>>>(in, out, a, tb);
@@ -251,15 +266,21 @@ static cudaError_t dst_launch_MV(const Plan& P, const TIO* in, TIO* out, int axi
 template <typename R, typename TIO, int M>
 static cudaError_t dst_launch_M(const Plan& P, const TIO* in, TIO* out, int axis, int nrhs,
                                 cudaStream_t s) {
-  // bit 0: radix-16 stage plan; bit 1: batched pre-processing loads; or the small tile
-  // (one warp, small_pairs(M) line pairs, radix-4 plan)
+  // bit 0: radix-16 stage plan; bit 1: batched pre-processing loads; bit 2: interleaved
+  // padded shared-memory layout; or the small tile (one warp, small_pairs(M) line
+  // pairs, radix-4 plan)
+  constexpr int NS = 2048 / M, NT = 128;
   if (P.dst_variant == DST_VARIANT_SMALL)
     return dst_launch_MV<R, TIO, M, 0, false, small_pairs(M), SMALL_NT>(P, in, out, axis, nrhs, s);
-  switch (P.dst_variant & 3) {
+  switch (P.dst_variant & 7) {
     case 0: return dst_launch_MV<R, TIO, M, 0, false>(P, in, out, axis, nrhs, s);
     case 1: return dst_launch_MV<R, TIO, M, 1, false>(P, in, out, axis, nrhs, s);
     case 2: return dst_launch_MV<R, TIO, M, 0, true>(P, in, out, axis, nrhs, s);
-    default: return dst_launch_MV<R, TIO, M, 1, true>(P, in, out, axis, nrhs, s);
+    case 3: return dst_launch_MV<R, TIO, M, 1, true>(P, in, out, axis, nrhs, s);
+    case 4: return dst_launch_MV<R, TIO, M, 0, false, NS, NT, 1>(P, in, out, axis, nrhs, s);
+    case 5: return dst_launch_MV<R, TIO, M, 1, false, NS, NT, 1>(P, in, out, axis, nrhs, s);
+    case 6: return dst_launch_MV<R, TIO, M, 0, true, NS, NT, 1>(P, in, out, axis, nrhs, s);
+    default: return dst_launch_MV<R, TIO, M, 1, true, NS, NT, 1>(P, in, out, axis, nrhs, s);
   }
 }
 

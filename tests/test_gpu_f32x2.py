@@ -143,7 +143,7 @@ def test_f32x2_dst_parity(d, N, monkeypatch):
     nt = 64
     x = W.random_field((nt, N ** d), seed=2500 + N + d)
     ref = OF.apply_space(x, OF.dst_matrix(N), d, N)
-    for dv in range(5):  # 4: the one-warp small-problem tile
+    for dv in range(9):  # 4..7: interleaved padded layout; 8: the one-warp small-problem tile
         monkeypatch.setenv("AAO_DST_VARIANT", str(dv))
         with aao.Solver(d, N, nt, 1.0 / nt, 0.1, precision=aao.AAO_PREC_F32X2) as s:
             xt = cu(x)

@@ -128,7 +128,7 @@ def test_dst_and_prec_variants(d, N, nt, monkeypatch):
     ref_dst = OF.apply_space(x, S, d, N)
     ref_prec = OF.ABACPreconditioner(d, N, nt, 1.0 / nt, ALPHA).apply(x)
     tol32 = gates.fp32("prec", d, N, nt, ALPHA)
-    for dv in range(5):  # 4: the one-warp small-problem tile
+    for dv in range(9):  # 4..7: interleaved padded layout; 8: the one-warp small-problem tile
         for tv in (1, 5, 30):
             monkeypatch.setenv("AAO_DST_VARIANT", str(dv))
             monkeypatch.setenv("AAO_TIME_VARIANT", f"{tv},{tv}")
