@@ -851,8 +851,12 @@ def run_served(args, world, rank, local, emit=True):
     lat = np.array([res["t_done"] - res["t_submit"] for _, res in ok])
     t_first = min(res["t_submit"] for _, res in ok)
     t_last = max(res["t_done"] for _, res in ok)
-    # each sampled result equals the same request solved alone (bit for bit)
+    # each sampled result equals the same request solved alone (bit for bit); served
+    # handles keep the standard tiles (their grouped launches use them), so the solo
+    # handles are created with them too
     same = True
+    small_env = os.environ.get("AAO_SMALL_TILES")
+    os.environ["AAO_SMALL_TILES"] = "0"
     for rid, (rr, xs) in sample.items():
         key = (rr["d"], rr["N"], rr["nt"])
         sh = shapes[key]
@@ -863,6 +867,10 @@ def run_served(args, world, rank, local, emit=True):
             s1.solve(b, x1, rtol=rr["tol"], maxit=100)
             torch.cuda.synchronize(dev)
             same &= bool(np.array_equal(x1.cpu().numpy(), xs))
+    if small_env is None:
+        del os.environ["AAO_SMALL_TILES"]
+    else:
+        os.environ["AAO_SMALL_TILES"] = small_env
     unknowns = sum(rr["nt"] * rr["N"] ** rr["d"] for rr, _ in ok)
     line = {
         "metric": f"served solves/s with p50/p99 latency (Poisson {rate:g}/s, mixed 1D/2D, 120 GB budget)",
