@@ -428,9 +428,7 @@ aao_status minres_enqueue_init(const MinresCtx& c, int use_x0, const MinresBufs&
   AAO_CK(cudaMemsetAsync(B.w, 0, vb, s));
   AAO_CK(cudaMemsetAsync(B.wp, 0, vb, s));
   AAO_TRY(c.prec(B.v, B.z));
-  AAO_KL(h, KC_DOT, s, launch_dot(P, B.z, B.v, p1, c.nrhs, s, nl));
-  AAO_KL(h, KC_DOT, s, launch_dot(P, c.bh, c.bh, p2, c.nrhs, s, nl));
-  AAO_KL(h, KC_DOT, s, launch_dot(P, B.v, B.v, p3, c.nrhs, s, nl));
+  AAO_KL(h, KC_DOT, s, launch_dot3(P, B.z, B.v, c.bh, c.bh, B.v, B.v, p1, p2, p3, c.nrhs, s, nl));
   AAO_KL(h, KC_SCAL, s, launch_scalars(0, h->sc, p1, nb_dot, p2, nb_dot, p3, nb_dot, c.nrhs, c.rtol,
                                        c.maxit, s, nl, c.prm));
   return AAO_OK;

@@ -195,6 +195,11 @@ int dot_blocks_per_rhs(const Plan& P);
 // partial[rhs*nb + b] = sum_i a_i*c_i over the rhs's n*m entries
 cudaError_t launch_dot(const Plan& P, const double* a, const double* c, double* partial, int nrhs,
                        cudaStream_t s, uint64_t* nl, const ScalarTail* tail = nullptr);
+// p1, p2, p3 = the partials of <a1, c1>, <a2, c2>, <a3, c3> in one pass, each bit for bit
+// launch_dot's
+cudaError_t launch_dot3(const Plan& P, const double* a1, const double* c1, const double* a2, const double* c2,
+                        const double* a3, const double* c3, double* p1, double* p2, double* p3, int nrhs,
+                        cudaStream_t s, uint64_t* nl);
 // y = a0*x0 + a1*x1 + a2*x2 with coefficients sc[rhs].cv (which = 0) ; x2 may be null
 cudaError_t launch_vupdate(const Plan& P, const double* T, const double* v, double* vprev_out,
                            const MinresScalars* sc, int nrhs, cudaStream_t s, uint64_t* nl);

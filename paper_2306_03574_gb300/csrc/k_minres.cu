@@ -54,6 +54,45 @@ __global__ void __launch_bounds__(VNT) k_dot(const double* __restrict__ a, const
   dot_body(a + rb, c + rb, partial + (long long)blockIdx.y * gridDim.x + blockIdx.x, len, blockIdx.x, gridDim.x);
 }
 
+// Three dot products in one pass (the initialisation's <z, v>, <b, b>, <v, v>): each
+// running sum takes the same elements in the same order as dot_body, and each block
+// reduction is dot_body's, so every partial is bit for bit that of a separate k_dot.
+__global__ void __launch_bounds__(VNT) k_dot3(const double* __restrict__ a1, const double* __restrict__ c1,
+                                              const double* __restrict__ a2, const double* __restrict__ c2,
+                                              const double* __restrict__ a3, const double* __restrict__ c3,
+                                              double* __restrict__ p1, double* __restrict__ p2,
+                                              double* __restrict__ p3, long long len) {
+  const long long rb = (long long)blockIdx.y * len;
+  const int bx = blockIdx.x, nbx = gridDim.x;
+  double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+  for (long long i = rb + (long long)bx * VNT + threadIdx.x; i < rb + len; i += (long long)nbx * VNT) {
+    s1 = fma(a1[i], c1[i], s1);
+    s2 = fma(a2[i], c2[i], s2);
+    s3 = fma(a3[i], c3[i], s3);
+  }
+  __shared__ double red[3][VNT / 32];
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  s3 = warp_sum(s3);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s1;
+    red[1][threadIdx.x >> 5] = s2;
+    red[2][threadIdx.x >> 5] = s3;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const long long o = (long long)blockIdx.y * nbx + bx;
+    double* outs[3] = {p1, p2, p3};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double t = (threadIdx.x < VNT / 32) ? red[k][threadIdx.x] : 0.0;
+      t = warp_sum(t);
+      if (threadIdx.x == 0) outs[k][o] = t;
+    }
+  }
+}
+
 // with a MINRES scalar step on the partials in the tail (minres_scalars.cuh); 8 resident
 // blocks per SM, the register budget of k_dot
 __global__ void __launch_bounds__(VNT, 8) k_dot_tail(const double* __restrict__ a, const double* __restrict__ c,
@@ -236,6 +275,15 @@ cudaError_t launch_dot(const Plan& P, const double* a, const double* c, double* 
   const dim3 g(dot_blocks_per_rhs(P), nrhs);
   if (tail) k_dot_tail<<<g, VNT, 0, s>>>(a, c, partial, (long long)P.n * P.m, *tail);
   else k_dot<<<g, VNT, 0, s>>>(a, c, partial, (long long)P.n * P.m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot3(const Plan& P, const double* a1, const double* c1, const double* a2, const double* c2,
+                        const double* a3, const double* c3, double* p1, double* p2, double* p3, int nrhs,
+                        cudaStream_t s, uint64_t* nl) {
+  if (nl) ++*nl;
+  k_dot3<<<dim3(dot_blocks_per_rhs(P), nrhs), VNT, 0, s>>>(a1, c1, a2, c2, a3, c3, p1, p2, p3,
+                                                           (long long)P.n * P.m);
   return cudaGetLastError();
 }
 
