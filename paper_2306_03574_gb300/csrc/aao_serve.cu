@@ -641,10 +641,21 @@ aao_status aao_serve_create(size_t hbm_budget_bytes, int max_slots, aao_server**
   s->max_slots = max_slots;
   s->t0 = Clock::now();
   cudaGetDevice(&s->device);
-  // streams and round buffers (pinned and device descriptors) of every size class
+  // streams and round buffers (pinned and device descriptors) of every size class.  The
+  // smaller the class, the higher its stream's priority: the CTAs of a small problem's
+  // kernels are dispatched ahead of the pending CTAs of a large problem's (a 1D request
+  // that solves in a third of a millisecond alone otherwise waits behind whole waves of
+  // a 2D time kernel); running CTAs are never preempted, and no result changes.
+  int prio_least = 0, prio_greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+    cudaGetLastError();
+    prio_least = prio_greatest = 0;
+  }
   bool ok = true;
-  for (SizeClass& C : s->cls) {
-    ok = ok && cudaStreamCreateWithFlags(&C.stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (int c = 0; c < NCLASS; ++c) {
+    SizeClass& C = s->cls[c];
+    const int prio = prio_greatest + ((prio_least - prio_greatest) * c) / (NCLASS - 1);
+    ok = ok && cudaStreamCreateWithPriority(&C.stream, cudaStreamNonBlocking, prio) == cudaSuccess;
     for (int i = 0; ok && i < ROUNDS_IN_FLIGHT; ++i) {
       Round* r = s->new_round();
       if (r) C.free_rounds.push_back(r);
