@@ -1387,7 +1387,7 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   }
   cudaStream_t s = 0;
   const size_t vb = h->vlen() * sizeof(double);
-  AAO_CK(cudaMemsetAsync(h->vv, 0, vb, s));
+  AAO_CK(launch_fill_test(h->vv, vb / sizeof(double), s));  // not zeros: see launch_fill_test
   cudaEvent_t e0, e1;
   AAO_CK(cudaEventCreate(&e0));
   AAO_CK(cudaEventCreate(&e1));
@@ -1441,9 +1441,11 @@ aao_status aao_autotune(aao_handle* h, const char* tune_file, int* chosen) {
   tvar(P, prec) = best_tv;
   for (size_t i = 0; i < dvs.size(); ++i) {
     P.dst_variant = dvs[i];
-    td[i] = timeit([&]() {
-      if (prec == AAO_PREC_F32X2 || prec == AAO_PREC_FP32_IR) launch_dst_axis_ff(P, h->vv, h->vz, 0, 1, s, nullptr);
-      else launch_dst_axis<double>(P, h->vv, h->vz, 0, 1, s, nullptr);
+    td[i] = timeit([&]() {  // every axis: a variant can suit the contiguous one only
+      for (int ax = 0; ax < P.d; ++ax) {
+        if (prec == AAO_PREC_F32X2 || prec == AAO_PREC_FP32_IR) launch_dst_axis_ff(P, h->vv, h->vz, ax, 1, s, nullptr);
+        else launch_dst_axis<double>(P, h->vv, h->vz, ax, 1, s, nullptr);
+      }
     });
   }
   const int best_dv = pick(dvs, td, def_dv);

@@ -200,6 +200,8 @@ cudaError_t launch_dot(const Plan& P, const double* a, const double* c, double* 
 cudaError_t launch_dot3(const Plan& P, const double* a1, const double* c1, const double* a2, const double* c2,
                         const double* a3, const double* c3, double* p1, double* p2, double* p3, int nrhs,
                         cudaStream_t s, uint64_t* nl);
+// y[i] = deterministic pseudo-random values in (-1, 1) (autotuner input)
+cudaError_t launch_fill_test(double* y, size_t count, cudaStream_t s);
 // y = a0*x0 + a1*x1 + a2*x2 with coefficients sc[rhs].cv (which = 0) ; x2 may be null
 cudaError_t launch_vupdate(const Plan& P, const double* T, const double* v, double* vprev_out,
                            const MinresScalars* sc, int nrhs, cudaStream_t s, uint64_t* nl);

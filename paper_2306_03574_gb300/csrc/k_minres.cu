@@ -287,6 +287,27 @@ cudaError_t launch_dot3(const Plan& P, const double* a1, const double* c1, const
   return cudaGetLastError();
 }
 
+// y[i] = a deterministic pseudo-random value in (-1, 1) (an integer hash of i): timing
+// input for the autotuner, whose kernels take shortcuts on zeros (the integer
+// conversions of the FP32 and double-float kernels return early for them).
+__global__ void __launch_bounds__(VNT) k_fill_test(double* __restrict__ y, long long len) {
+  for (long long i = (long long)blockIdx.x * VNT + threadIdx.x; i < len; i += (long long)gridDim.x * VNT) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull;
+    z ^= z >> 29;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 32;
+    y[i] = (double)(long long)(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+}
+
+cudaError_t launch_fill_test(double* y, size_t count, cudaStream_t s) {
+  long long nb = ((long long)count + VNT - 1) / VNT;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  k_fill_test<<<(unsigned)nb, VNT, 0, s>>>(y, (long long)count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vupdate(const Plan& P, const double* T, const double* v, double* vprev_out,
                            const MinresScalars* sc, int nrhs, cudaStream_t s, uint64_t* nl) {
   if (nl) ++*nl;
