@@ -608,9 +608,21 @@ aao_status build_graph(const MinresCtx& c, int use_x0, cudaGraphExec_t* out) {
 // preconditioner the full P_alpha^{-1}; used for a variable coefficient).
 // With graphs enabled (and kernel timing off) the loop runs on the device from one
 // captured graph per (batch size, mode); bh and xh must then be handle workspace.
+// Graph path, after the stream has reached the end of the launched graph: count its
+// kernels and read the scalars copied to the host.
+aao_status minres_finish_graph(aao_handle* h, int nrhs, aao_solve_info* info) {
+  // kernels the graph ran: the initialisation plus one body per loop trip
+  h->launches += h->last_init_kernels + (uint64_t)(*h->trips_host) * h->last_body_kernels;
+  return minres_collect(h, nrhs, info);
+}
+
+// deferred (graph path only; may be null): enqueue the solve and the copies of its
+// scalars and return with *deferred = true; the caller synchronises s (after enqueuing
+// more work of its own) and then calls minres_finish_graph.  One host round trip per
+// solve instead of two.
 aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_x0, int nrhs,
                            double rtol, int maxit, aao_solve_info* info, cudaStream_t s, bool true_res,
-                           bool physical = false) {
+                           bool physical = false, bool* deferred = nullptr) {
   MinresCtx c{h, bh, xh, nrhs, rtol, maxit, s, true_res, physical};
   const size_t scb = (size_t)nrhs * sizeof(MinresScalars);
   const MinresBufs B0{h->vv, h->vvp, h->vz, h->vzn, h->vw, h->vwp};
@@ -627,10 +639,12 @@ aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_
     AAO_CK(cudaGraphLaunch(ex, s));
     AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
     AAO_CK(cudaMemcpyAsync(h->trips_host, h->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (deferred) {
+      *deferred = true;
+      return AAO_OK;
+    }
     AAO_CK(cudaStreamSynchronize(s));
-    // kernels the graph ran: the initialisation plus one body per loop trip
-    h->launches += h->last_init_kernels + (uint64_t)(*h->trips_host) * h->last_body_kernels;
-    return minres_collect(h, nrhs, info);
+    return minres_finish_graph(h, nrhs, info);
   }
   AAO_TRY(minres_enqueue_init(c, use_x0, B0));
   AAO_CK(cudaMemcpyAsync(h->sc_host, h->sc, scb, cudaMemcpyDeviceToHost, s));
@@ -651,8 +665,10 @@ aao_status minres_spectral(aao_handle* h, const double* bh, double* xh, int use_
 }
 
 // ||b - Y T x|| / ||b|| per rhs in the physical basis (stencil), copied into info.
-aao_status physical_check(aao_handle* h, const double* b, const double* x, int nrhs, double rtol,
-                          aao_solve_info* info, aao_status* worst, cudaStream_t s) {
+// The physical residual check in two halves: the kernels and the copy of the relative
+// residuals to the host (stream-ordered), then, after the stream is synchronised, the
+// residuals into info and the status.
+aao_status physical_check_enqueue(aao_handle* h, const double* b, const double* x, int nrhs, cudaStream_t s) {
   double* p1 = h->partial;
   double* p2 = h->partial + (size_t)h->nrhs_max * h->partial_stride;
   int nb = 0;
@@ -661,12 +677,22 @@ aao_status physical_check(aao_handle* h, const double* b, const double* x, int n
   AAO_KL(h, KC_SCAL, s, launch_relres(p1, nb, p2, dot_blocks_per_rhs(h->P), h->relres_dev, nrhs, s,
                                       &h->launches));
   AAO_CK(cudaMemcpyAsync(h->relres_host, h->relres_dev, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-  AAO_CK(cudaStreamSynchronize(s));
+  return AAO_OK;
+}
+
+void physical_check_finish(aao_handle* h, int nrhs, double rtol, aao_solve_info* info, aao_status* worst) {
   for (int r = 0; r < nrhs; ++r) {
     if (info) info[r].relres_true = h->relres_host[r];
     if (h->relres_host[r] > rtol && *worst == AAO_OK) *worst = AAO_ENOTCONV;
     if (info && h->relres_host[r] > rtol && info[r].status == AAO_OK) info[r].status = AAO_ENOTCONV;
   }
+}
+
+aao_status physical_check(aao_handle* h, const double* b, const double* x, int nrhs, double rtol,
+                          aao_solve_info* info, aao_status* worst, cudaStream_t s) {
+  AAO_TRY(physical_check_enqueue(h, b, x, nrhs, s));
+  AAO_CK(cudaStreamSynchronize(s));
+  physical_check_finish(h, nrhs, rtol, info, worst);
   return AAO_OK;
 }
 
@@ -688,9 +714,15 @@ aao_status solve_fp64(aao_handle* h, const double* b, double* x, int use_x0, int
   }
   AAO_TRY(dst_apply(h, b, h->vbh, nrhs, s));
   if (use_x0) AAO_TRY(dst_apply(h, x, h->vxh, nrhs, s));
-  aao_status worst = minres_spectral(h, h->vbh, h->vxh, use_x0, nrhs, rtol, maxit, inf, s, true);
+  // graph path: the solve, the inverse DSTs and the physical check are enqueued back to
+  // back and the host waits once
+  bool deferred = false;
+  aao_status worst = minres_spectral(h, h->vbh, h->vxh, use_x0, nrhs, rtol, maxit, inf, s, true, false, &deferred);
   AAO_TRY(dst_apply(h, h->vxh, x, nrhs, s));
-  AAO_TRY(physical_check(h, b, x, nrhs, rtol, inf, &worst, s));
+  AAO_TRY(physical_check_enqueue(h, b, x, nrhs, s));
+  AAO_CK(cudaStreamSynchronize(s));
+  if (deferred) worst = minres_finish_graph(h, nrhs, inf);
+  physical_check_finish(h, nrhs, rtol, inf, &worst);
   if (worst != AAO_OK) g_err = std::string("MINRES: ") + aao_status_str(worst);
   return worst;
 }
