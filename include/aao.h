@@ -280,8 +280,12 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
  * method.  Each request is a solve of eq. (precsys) as aao_minres_solve does it in
  * the request's precision (FP64 or double-float; zero initial guess, true relative
  * residual <= rtol); the Krylov state stays on
- * the device for the whole solve (graph-captured loop); a request never shares
- * buffers with another, so its result does not depend on what else is running.
+ * the device for the whole solve, whose iterations run in grouped launches with the
+ * other requests of its size class (one CUDA stream per class, the smaller classes at
+ * the higher stream priorities); a request never shares buffers with another and its
+ * blocks run the code and decomposition of its solo solve, so its result does not
+ * depend on what else is running (bit for bit the solo solve of a handle created with
+ * AAO_SMALL_TILES=0: served handles keep the standard tiles).
  * --------------------------------------------------------------------------- */
 typedef struct aao_server aao_server;
 
