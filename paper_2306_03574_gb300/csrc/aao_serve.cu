@@ -54,6 +54,7 @@ constexpr int NCLASS = 4;             // size classes
 constexpr int ROUNDS_IN_FLIGHT = 3;   // rounds queued per class
 constexpr int NBUCKET = 5;            // time lengths 64 .. 1024
 constexpr int QUEUE_SCAN = 256;       // first-fit scan depth of the queue
+constexpr int LARGE_ACTIVE = 2;       // requests active at once in the largest class
 
 int size_class(long long unknowns) {
   if (unknowns < (1LL << 18)) return 0;
@@ -272,6 +273,11 @@ struct aao_server {
     const aao_request& q = p.req;
     const int c = size_class(unknowns_of(q));
     if ((int)cls[c].active.size() >= GROUP_MAX) return false;
+    // the largest class runs at most LARGE_ACTIVE requests at a time: each round of a
+    // class runs one iteration of all its requests, and a GPU-filling request gains
+    // nothing from sharing its rounds, while the requests behind it in the queue wait
+    // the shorter for it (first come, first served within the class)
+    if (c == NCLASS - 1 && (int)cls[c].active.size() >= LARGE_ACTIVE) return false;
     PoolEntry* pe = nullptr;
     {
       std::lock_guard<std::mutex> lk(pool_mu);
