@@ -8,8 +8,10 @@
 // the producer: each block, after writing its partial, counts itself in with an atomic;
 // the last block of a right-hand side to arrive runs the step on the partials with the
 // same code and order, so both give the same bits.  A step fused this way removes a
-// launch from every MINRES iteration (the latency of small problems is launch-bound).
-// Nothing waits: a block that is not last simply exits.
+// launch from every MINRES iteration; the last block's fence, atomic and dependent
+// partial reads form a serial chain of a few microseconds, about what a kernel node of
+// the captured graph costs on GB300, so the fused form is an option (AAO_FUSED_SCALARS)
+// rather than the default.  Nothing waits: a block that is not last simply exits.
 #pragma once
 
 #include "aao_internal.cuh"
