@@ -729,8 +729,12 @@ aao_status solve_fp64(aao_handle* h, const double* b, double* x, int use_x0, int
 
 // Mixed precision: FP64 iterative refinement in the DST basis around MINRES whose
 // preconditioner (the time pipeline) runs in FP32/complex64.
+// bh_ready (DST basis, zero initial guess): b^ is already in the handle's b^ vector (the
+// pipelined host-buffer solve transformed it chunk by chunk); the call then ends with x^
+// in the handle's x^ vector and the refinement status, and the caller runs the inverse
+// DSTs and the physical check.
 aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int nrhs, double rtol,
-                    int maxit, aao_solve_info* info, cudaStream_t s) {
+                    int maxit, aao_solve_info* info, cudaStream_t s, bool bh_ready = false) {
   const Plan& P = h->P;
   const size_t vb = (size_t)nrhs * h->vlen() * sizeof(double);
   double* p1 = h->partial;
@@ -742,7 +746,9 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
   std::vector<aao_solve_info> inner(nrhs), loc(nrhs);
   aao_solve_info* acc = info ? info : loc.data();
   for (int r = 0; r < nrhs; ++r) acc[r] = aao_solve_info{0, AAO_ENOTCONV, 1.0, 1.0, 0, 0};
-  if (!phys) {
+  if (bh_ready) {
+    if (phys || use_x0) return fail(AAO_EINVAL, "internal: pre-transformed refinement solve");
+  } else if (!phys) {
     AAO_TRY(dst_apply(h, b, bh, nrhs, s));
     if (use_x0) AAO_TRY(dst_apply(h, x, xh, nrhs, s));
   } else {
@@ -805,11 +811,12 @@ aao_status solve_ir(aao_handle* h, const double* b, double* x, int use_x0, int n
                                         h->vlen(), s, nl));
     }
   }
-  if (!phys) AAO_TRY(dst_apply(h, xh, x, nrhs, s));
-  else AAO_CK(cudaMemcpyAsync(x, xh, vb, cudaMemcpyDeviceToDevice, s));
   aao_status worst = AAO_OK;
   for (int r = 0; r < nrhs; ++r)
     if (acc[r].status != AAO_OK && worst == AAO_OK) worst = (aao_status)acc[r].status;
+  if (bh_ready) return worst;
+  if (!phys) AAO_TRY(dst_apply(h, xh, x, nrhs, s));
+  else AAO_CK(cudaMemcpyAsync(x, xh, vb, cudaMemcpyDeviceToDevice, s));
   AAO_TRY(physical_check(h, b, x, nrhs, rtol, acc, &worst, s));
   if (worst != AAO_OK)
     g_err = std::string("MINRES (FP32 preconditioner + FP64 refinement): ") + aao_status_str(worst);
@@ -1632,7 +1639,7 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
   const size_t pb = (size_t)nrhs * P.m * sizeof(double);
   double* d_psi0 = h->hs_psi;
   double* d_psi1 = h->hs_psi + (size_t)h->nrhs_max * P.m;
-  if (h->var_on || h->precision == AAO_PREC_FP32_IR) {  // whole-vector copies around the solve
+  if (h->var_on) {  // physical-basis solve: whole-vector copies around it
     AAO_CK(cudaMemcpyAsync(h->hs_f, f, vb, cudaMemcpyHostToDevice, s));
     AAO_CK(cudaMemcpyAsync(d_psi0, psi0, pb, cudaMemcpyHostToDevice, s));
     AAO_CK(cudaMemcpyAsync(d_psi1, psi1, pb, cudaMemcpyHostToDevice, s));
@@ -1693,7 +1700,10 @@ aao_status aao_solve_host(aao_handle* h, const double* f, const double* psi0, co
   AAO_TRY(join(ev[2 * nch + 3], ev[2 * nch + 4]));
   std::vector<aao_solve_info> loc(nrhs);
   aao_solve_info* inf = info ? info : loc.data();
-  aao_status worst = minres_spectral(h, h->vbh, h->vxh, 0, nrhs, rtol, maxit, inf, s, true);
+  aao_status worst = h->precision == AAO_PREC_FP32_IR
+                         ? solve_ir(h, nullptr, nullptr, 0, nrhs, rtol, maxit, inf, s, true)
+                         : minres_spectral(h, h->vbh, h->vxh, 0, nrhs, rtol, maxit, inf, s, true);
+  if (worst != AAO_OK && worst != AAO_ENOTCONV && worst != AAO_EBREAKDOWN) return worst;
   AAO_TRY(fork(ev[2 * nch + 5]));
   for (int c = 0; c < nch; ++c) {
     const size_t off = (size_t)(c / per) * P.n * P.m + (size_t)(c % per) * CH * P.m;
